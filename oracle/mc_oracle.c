@@ -21,7 +21,7 @@
  *                Lambda(x) = prod_{j=1}^{q} (1 + x/xi_j), xi_j = (t_n - t_{n-j}) / h
  *   corrector    G(e) = h f(z_0 + e) - z_1 - l_1 e = 0, modified Newton with
  *                P = I - gamma J, gamma = h / l_1
- *   error        est_q = (1 - l_1 / S) e,  S = sum_{i=1}^{q+1} 1/xi_i
+ *   error        est_q = e (1/xi_{q+1}) / l_1
  *
  * Each function below names what it follows. Pins (tests/test_oracle_*.py):
  * Robertson values at t = 40, the A->B->C closed form, element and energy
@@ -176,7 +176,7 @@ void or_lu_solve(int n, const double *lu, const int *piv, double *b)
 }
 
 /* ------------------------------------------------------------------------ */
-/* BDF coefficients (paper silent; restated from the FLC BDF mathematics).  */
+/* BDF coefficients (paper silent; restated from the BDF mathematics).      */
 /* ------------------------------------------------------------------------ */
 
 /* xi_j = (sum of the first j gaps) / h, j = 1..m, written to xi[0..m-1]. The
@@ -193,11 +193,16 @@ void or_xi_from_gaps(double h, const double *gaps, int m, double *xi)
 /* Corrector vector l[0..q] of the variable-coefficient BDF of order q: the
    coefficients of Lambda(x) = prod_{j=1}^{q} (1 + x/xi_j), which vanishes at
    the q previous points, so that P_n = P_{n-1} + e Lambda keeps interpolating
-   the last q+1 values; l_1 = sum_{j<=q} 1/xi_j. Also returns the local-error
-   coefficient cq: if the solution is a polynomial of degree q+1 and the
-   history lies on it, the true local error of the step is
-   e (1 - l_1/S), S = sum_{i=1}^{q+1} 1/xi_i, i.e. cq = (1/xi_{q+1}) / S > 0.
-   xi[0..q] holds xi_1..xi_{q+1}. */
+   the last q+1 values; l_1 = sum_{j<=q} 1/xi_j.
+
+   Also returns the local-error coefficient cq. For a solution that is a
+   polynomial of degree q+1 with leading coefficient a, the predictor misses
+   y(t_n) by d = a prod_{j=1}^{q+1}(t_n - t_{n-j}), and one step from exact back
+   values has local error d (S/l_1 - 1) = d (1/xi_{q+1}) / l_1,
+   S = sum_{i<=q+1} 1/xi_i. Once earlier local errors have settled into a smooth
+   global error the correction e of a step equals that predictor miss, so the
+   error estimate is cq e with cq = (1/xi_{q+1}) / l_1; at constant steps this is
+   the textbook constant 1/((q+1) G_q). xi[0..q] holds xi_1..xi_{q+1}. */
 void or_bdf_coeffs(int q, const double *xi, double *l, double *cq)
 {
     double poly[OR_QMAX + 2];
@@ -208,8 +213,7 @@ void or_bdf_coeffs(int q, const double *xi, double *l, double *cq)
         for (int k = j; k >= 1; --k) poly[k] += c * poly[k - 1];
     }
     for (int k = 0; k <= q; ++k) l[k] = poly[k];
-    double last = 1.0 / xi[q];
-    *cq = last / (l[1] + last);
+    *cq = (1.0 / xi[q]) / l[1];
 }
 
 /* Coefficient c with est_{q-1} = c z_q: the local error an order q-1 step of
@@ -228,14 +232,13 @@ double or_err_coef_qm1(int q, const double *xi)
     return prod / l1;
 }
 
-/* Coefficient c with est_{q+1} = c (e_n - (h_n/h_{n-1})^{q+1} e_{n-1}): at
-   constant steps e_n ~ (G_{q+1}/G_q) h^{q+1} y^(q+1), so the difference of
-   two corrections estimates (G_{q+1}/G_q) h^{q+2} y^(q+2), and the order q+1
-   local error is h^{q+2} y^(q+2) / ((q+2) G_{q+1}). */
+/* Coefficient c with est_{q+1} = c (e_n - (h_n/h_{n-1})^{q+1} e_{n-1}): with
+   e_n ~ h^{q+1} y^(q+1) (the settled correction above), the difference of two
+   corrections estimates h^{q+2} y^(q+2), and the order q+1 local error is
+   h^{q+2} y^(q+2) / ((q+2) G_{q+1}). */
 double or_err_coef_qp1(int q)
 {
-    double gq = harmonic(q), gq1 = harmonic(q + 1);
-    return gq / ((double)(q + 2) * gq1 * gq1);
+    return 1.0 / ((double)(q + 2) * harmonic(q + 1));
 }
 
 /* Order rise q -> q+1: the degree q+1 polynomial Q through the new value and
