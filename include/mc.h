@@ -1,0 +1,219 @@
+/*
+ * mc.h -- C ABI of the B300 per-cell burn library (libmc.so).
+ *
+ * The operation. A "burn" integrates one zone's reaction network over an
+ * operator-split step dt, independently in every cell, with a VODE-style
+ * variable-order BDF integrator, caps the number of steps and hands any
+ * failure back to the caller as a per-cell status (paper: Software design
+ * section, paragraphs 2-4 -- single-zone routines applied over all zones on the
+ * GPU, state resident in GPU memory, step cap and failure pass-back, network
+ * separate from the integrator, operator-split coupling). The BDF details
+ * (variable-coefficient Nordsieck form, modified Newton on I - gamma J,
+ * local-error step and order control) are the library's reading of the VODE
+ * method the paper cites (Brown, Byrne & Hindmarsh 1989).
+ *
+ * The network. Species x_i are number fractions (n_i / n, n = total density
+ * in cm^-3, held fixed during the burn). Reaction r turns up to two
+ * reactant species into up to two product species; each direction has a rate
+ * coefficient k = A T^b exp(-C/T) (cm^3/s for two-body, 1/s for one-body), and
+ * the forward direction releases dE_eV[r] electron-volts. With energy_eq set,
+ * the state also carries the thermal energy per particle-density unit
+ * u = (sum x) k_B T / (gamma - 1) and T is recovered from it by the ideal-gas
+ * EOS; without it the burn is isothermal at the cell's T (or T = 1 when T is
+ * NULL).
+ *
+ * Memory. Every cell array is structure-of-arrays: x[i * ld + c] is species i
+ * of cell c, rate_scale[r * ld + c] the factor of reaction r, stats[k * ld + c]
+ * counter k. Arrays are device pointers unless stated otherwise; mc_burn_batch
+ * also accepts host pointers (it then stages through library memory and
+ * returns after the results are back on the host). The caller owns every cell
+ * array; the library owns network constants, scratch and the serving pool.
+ *
+ * Errors. Calls return an mc_status: MC_OK, or a negative code for bad
+ * arguments, allocation or CUDA failures (the message is in mc_last_error(),
+ * per thread). A cell whose integration fails is not an error: its status[c]
+ * says why and the call still returns MC_OK.
+ *
+ * Threads and streams. Batch calls are asynchronous on the caller's stream
+ * (cudaStream_t passed as void*; NULL = legacy default stream). Network
+ * handles are immutable after creation and may be shared by threads. Server
+ * calls are thread-safe.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mc_status;
+#define MC_OK 0
+#define MC_PENDING 1
+#define MC_E_INVALID (-1)     /* bad argument */
+#define MC_E_NOMEM (-2)       /* device or host allocation failed */
+#define MC_E_CUDA (-3)        /* a CUDA call failed */
+#define MC_E_BUSY (-4)        /* resource in use (e.g. a server still draining) */
+#define MC_E_TIMEOUT (-5)     /* a bounded wait ran out */
+#define MC_E_NOTFOUND (-6)    /* unknown request id */
+#define MC_E_BUDGET (-7)      /* a request can never fit the memory budget */
+#define MC_E_UNSUPPORTED (-8) /* network shape outside the compiled range */
+
+/* per-cell status (status[c]) */
+#define MC_CELL_OK 0
+#define MC_CELL_MAX_STEPS 1   /* step cap reached (the state is at the last accepted time) */
+#define MC_CELL_H_UNDERFLOW 2 /* step size fell below the resolution of t */
+#define MC_CELL_CONV_FAIL 3   /* 10 consecutive Newton failures */
+#define MC_CELL_BAD_INPUT 4   /* non-finite input, T <= 0, n <= 0, or f(y0) not finite */
+#define MC_CELL_NONFINITE 5   /* the state stopped being finite */
+
+/* per-cell counters (stats[k * ld + c]) */
+#define MC_STAT_STEPS 0       /* accepted steps */
+#define MC_STAT_ERR_FAILS 1   /* local-error test failures */
+#define MC_STAT_CONV_FAILS 2  /* Newton failures that cut the step */
+#define MC_STAT_RHS 3         /* right-hand side evaluations */
+#define MC_STAT_JAC 4         /* Jacobian evaluations */
+#define MC_STAT_LU 5          /* iteration-matrix factorisations */
+#define MC_STAT_NEWTON 6      /* Newton corrections (linear solves) */
+#define MC_STAT_ORDER 7       /* BDF order at the end */
+#define MC_NSTAT 8
+
+/* integrator variants (mc_burn_opts.variant) */
+#define MC_VARIANT_AUTO 0       /* autotuner's choice */
+#define MC_VARIANT_PLAIN 1      /* one thread per cell, one launch over the cells */
+#define MC_VARIANT_PERSISTENT 2 /* persistent workers pulling cells from a queue */
+
+typedef struct mc_network mc_network;
+typedef struct mc_server mc_server;
+typedef struct mc_graph mc_graph;
+
+/* Network description, read by mc_network_create (which copies it).
+ * react/prod: [n_reactions][2] species indices, -1 for an empty slot (slot 0
+ * must be used). A_f..C_r, dE_eV: [n_reactions]. A = 0 disables a direction.
+ * n_species + (energy_eq ? 1 : 0) must be <= 40 and n_reactions <= 512. */
+typedef struct {
+    int32_t n_species;
+    int32_t n_elements;   /* informational */
+    int32_t n_reactions;
+    int32_t energy_eq;    /* 1: carry the energy equation (ideal gas) */
+    const int32_t *react;
+    const int32_t *prod;
+    const double *A_f, *b_f, *C_f;
+    const double *A_r, *b_r, *C_r;
+    const double *dE_eV;
+    double gamma;         /* ratio of specific heats (energy_eq only) */
+} mc_network_desc;
+
+/* Integration options. Use mc_burn_opts_default() and override fields. */
+typedef struct {
+    double rtol;            /* relative tolerance (default 1e-6) */
+    double atol;            /* absolute tolerance (default 1e-10) */
+    int32_t max_order;      /* highest BDF order, 1..5 (default 5) */
+    int32_t max_steps;      /* step cap per cell, counting rejected attempts (default 100000) */
+    int32_t lu_precision;   /* 64: FP64 iteration matrix; 32: FP32 matrix and LU,
+                               FP64 residual/history/norm, failed cells retried in FP64 */
+    int32_t variant;        /* MC_VARIANT_* */
+    int32_t block_threads;  /* threads per block, 0 = autotuned */
+    int32_t blocks_per_sm;  /* persistent grid = blocks_per_sm x SMs, 0 = autotuned */
+} mc_burn_opts;
+
+void mc_burn_opts_default(mc_burn_opts *opts);
+
+/* Upload a network. The description is copied; the handle stays valid until
+ * mc_network_destroy. Errors: MC_E_INVALID (bad indices or sizes),
+ * MC_E_UNSUPPORTED (too many ODEs or reactions), MC_E_NOMEM, MC_E_CUDA. */
+mc_status mc_network_create(const mc_network_desc *desc, mc_network **out);
+mc_status mc_network_destroy(mc_network *net);
+int32_t mc_network_n_ode(const mc_network *net);
+
+/* Burn n_cells cells over dt (seconds) in place.
+ *   x          [n_species][ld] in/out number fractions
+ *   T          [ld] in/out temperature (K); required when energy_eq, else the
+ *              isothermal temperature of each cell or NULL (T = 1)
+ *   ndens      [ld] total density (cm^-3) or NULL (n = 1)
+ *   rate_scale [n_reactions][ld] per-cell factor on both directions, or NULL
+ *   status     [ld] out per-cell MC_CELL_* code
+ *   stats      [MC_NSTAT][ld] out counters, or NULL
+ *   stream     cudaStream_t or NULL
+ * ld >= n_cells. Device pointers: asynchronous, returns after the launch.
+ * Host pointers (all cell arrays on the host): synchronous round trip through
+ * library device memory. Errors: MC_E_INVALID, MC_E_NOMEM, MC_E_CUDA. */
+mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
+                        double dt, double *x, int64_t ld, double *T, const double *ndens,
+                        const double *rate_scale, int32_t *status, int32_t *stats,
+                        void *stream);
+
+/* One segment of a mixed batch: cells that share a network, laid out as in
+ * mc_burn_batch (device pointers). */
+typedef struct {
+    const mc_network *net;
+    int64_t n_cells;
+    int64_t ld;
+    double *x;
+    double *T;
+    const double *ndens;
+    const double *rate_scale;
+    int32_t *status;
+    int32_t *stats;
+} mc_segment;
+
+/* Burn several segments (different networks, uneven stiffness) in ONE
+ * persistent launch: workers pull cells from per-network queues, and a lane
+ * whose cell finishes takes the next cell (paper: divergence between zones,
+ * Software design section, paragraph 3). Asynchronous on stream. */
+mc_status mc_burn_mixed(const mc_segment *segs, int32_t n_segs, const mc_burn_opts *opts,
+                        double dt, void *stream);
+
+/* Capture mc_burn_mixed for fixed segments into a CUDA graph (queue reset,
+ * persistent launch, counter reduction) and replay it with mc_graph_launch.
+ * The segment arrays must stay allocated while the graph exists; their
+ * contents may change between launches. totals (may be NULL) receives, after
+ * each replay, the MC_NSTAT counters summed over all cells (device int64[8]). */
+mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, const mc_burn_opts *opts,
+                          double dt, int64_t *totals, void *stream, mc_graph **out);
+mc_status mc_graph_launch(mc_graph *g, void *stream);
+mc_status mc_graph_destroy(mc_graph *g);
+
+/* ---------------------------------------------------------------- serving */
+/* A server keeps burn requests' state in a device pool, admits requests in
+ * arrival order while the pool's bytes stay within hbm_budget_bytes, burns
+ * admitted work in bounded persistent epochs on its own stream (requests that
+ * arrive while others run join the next epoch, so their work overlaps on the
+ * device) and copies results back to the caller's buffers. */
+typedef struct {
+    int32_t state;          /* MC_PENDING or MC_OK */
+    int32_t n_failed;       /* cells with status != MC_CELL_OK */
+    int64_t n_cells;
+    double t_submit;        /* seconds on the server's monotonic clock */
+    double t_admit;
+    double t_done;
+} mc_request_info;
+
+mc_status mc_server_create(int32_t device, uint64_t hbm_budget_bytes, const mc_burn_opts *opts,
+                           mc_server **out);
+/* Queue a request. Cell arrays as in mc_burn_batch (host or device memory;
+ * rate_scale is not supported here). The caller must not touch them until
+ * mc_request_poll reports MC_OK. Never blocks on the GPU. Errors:
+ * MC_E_BUDGET if the request alone exceeds the budget, MC_E_INVALID. */
+mc_status mc_request_submit(mc_server *srv, const mc_network *net, int64_t n_cells, double dt,
+                            double *x, int64_t ld, double *T, const double *ndens,
+                            int32_t *status, uint64_t *req_id);
+/* MC_PENDING while in flight, MC_OK once results are in the caller's buffers
+ * (info filled in either case when non-NULL), MC_E_NOTFOUND otherwise. */
+mc_status mc_request_poll(mc_server *srv, uint64_t req_id, mc_request_info *info);
+/* Wait (bounded by timeout_s) until every submitted request is done. */
+mc_status mc_server_drain(mc_server *srv, double timeout_s);
+/* Drain (bounded, 600 s) and free. MC_E_TIMEOUT if work was still running. */
+mc_status mc_server_destroy(mc_server *srv);
+
+/* ---------------------------------------------------------------- misc */
+const char *mc_last_error(void);
+int32_t mc_version(void);
+/* Kernel launches issued by this thread since the last reset (for accounting). */
+int64_t mc_launch_count(int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

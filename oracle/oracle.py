@@ -22,17 +22,32 @@ _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, fma: bool = False) -> str:
     """Compile mc_oracle.c into _build/libmc_oracle.so (plain IEEE double:
-    -O2, no fast-math, no FMA contraction)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        tmp = _OUT + f".tmp{os.getpid()}"
+    -O2, no fast-math, no FMA contraction). fma=True builds the same source
+    with FMA contraction into a separate library: a rounding twin used only to
+    calibrate the parity rule."""
+    out = _OUT.replace(".so", "_fma.so") if fma else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        flags = ["-mfma", "-ffp-contract=fast"] if fma else ["-ffp-contract=off"]
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-fno-fast-math", "-Wall", "-o", tmp, _SRC,
-                               "-lm", "-lpthread"])
-        os.replace(tmp, _OUT)
-    return _OUT
+                               "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm", "-lpthread"] + flags)
+        os.replace(tmp, out)
+    return out
+
+
+def rounding_twin():
+    """A second, independent instance of this module bound to the FMA-contracted
+    build of the same oracle source (same algorithm, different rounding)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("oracle_fma_twin", __file__)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    path = build(fma=True)
+    mod.build = lambda force=False, fma=False: path
+    return mod
 
 
 def lib():

@@ -1,0 +1,264 @@
+"""ctypes binding of libmc.so with the C ABI's names (include/mc.h).
+
+Argument marshalling only: every step of the burn runs in the library's CUDA
+kernels. Cell arrays may be torch CUDA tensors (device path, asynchronous on
+the given stream) or numpy arrays / CPU tensors (host path, synchronous). If
+libmc.so is missing or cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2608_06466_b300.build` "
+                      "(there is no CPU fallback)")
+lib = C.CDLL(LIB_PATH)
+
+MC_OK, MC_PENDING = 0, 1
+ERRORS = {-1: "MC_E_INVALID", -2: "MC_E_NOMEM", -3: "MC_E_CUDA", -4: "MC_E_BUSY", -5: "MC_E_TIMEOUT",
+          -6: "MC_E_NOTFOUND", -7: "MC_E_BUDGET", -8: "MC_E_UNSUPPORTED"}
+CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "conv_fail", 4: "bad_input", 5: "nonfinite"}
+STAT_NAMES = ["steps", "err_fails", "conv_fails", "rhs", "jac", "lu", "newton", "order"]
+MC_NSTAT = 8
+MC_VARIANT_AUTO, MC_VARIANT_PLAIN, MC_VARIANT_PERSISTENT = 0, 1, 2
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class mc_network_desc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_elements", C.c_int32), ("n_reactions", C.c_int32),
+                ("energy_eq", C.c_int32), ("react", _ip), ("prod", _ip),
+                ("A_f", _dp), ("b_f", _dp), ("C_f", _dp), ("A_r", _dp), ("b_r", _dp), ("C_r", _dp),
+                ("dE_eV", _dp), ("gamma", C.c_double)]
+
+
+class mc_burn_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_order", C.c_int32),
+                ("max_steps", C.c_int32), ("lu_precision", C.c_int32), ("variant", C.c_int32),
+                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+class mc_segment(C.Structure):
+    _fields_ = [("net", C.c_void_p), ("n_cells", C.c_int64), ("ld", C.c_int64), ("x", C.c_void_p),
+                ("T", C.c_void_p), ("ndens", C.c_void_p), ("rate_scale", C.c_void_p),
+                ("status", C.c_void_p), ("stats", C.c_void_p)]
+
+
+class mc_request_info(C.Structure):
+    _fields_ = [("state", C.c_int32), ("n_failed", C.c_int32), ("n_cells", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+def _sig(name, res, args):
+    f = getattr(lib, name, None)
+    if f is None:
+        return None
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("mc_burn_opts_default", None, [C.POINTER(mc_burn_opts)])
+_sig("mc_network_create", C.c_int32, [C.POINTER(mc_network_desc), C.POINTER(C.c_void_p)])
+_sig("mc_network_destroy", C.c_int32, [C.c_void_p])
+_sig("mc_network_n_ode", C.c_int32, [C.c_void_p])
+_sig("mc_burn_batch", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p,
+                                  C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p])
+_sig("mc_burn_mixed", C.c_int32, [C.POINTER(mc_segment), C.c_int32, C.POINTER(mc_burn_opts), C.c_double,
+                                  C.c_void_p])
+_sig("mc_graph_create", C.c_int32, [C.POINTER(mc_segment), C.c_int32, C.POINTER(mc_burn_opts), C.c_double,
+                                    C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)])
+_sig("mc_graph_launch", C.c_int32, [C.c_void_p, C.c_void_p])
+_sig("mc_graph_destroy", C.c_int32, [C.c_void_p])
+_sig("mc_server_create", C.c_int32, [C.c_int32, C.c_uint64, C.POINTER(mc_burn_opts), C.POINTER(C.c_void_p)])
+_sig("mc_request_submit", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int64,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)])
+_sig("mc_request_poll", C.c_int32, [C.c_void_p, C.c_uint64, C.POINTER(mc_request_info)])
+_sig("mc_server_drain", C.c_int32, [C.c_void_p, C.c_double])
+_sig("mc_server_destroy", C.c_int32, [C.c_void_p])
+_sig("mc_last_error", C.c_char_p, [])
+_sig("mc_version", C.c_int32, [])
+_sig("mc_launch_count", C.c_int64, [C.c_int32])
+
+
+class MCError(RuntimeError):
+    pass
+
+
+def check(rc: int, what: str = "") -> int:
+    if rc < 0:
+        msg = lib.mc_last_error().decode(errors="replace")
+        raise MCError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
+    return rc
+
+
+def mc_last_error() -> str:
+    return lib.mc_last_error().decode(errors="replace")
+
+
+def mc_burn_opts_default(**over) -> mc_burn_opts:
+    o = mc_burn_opts()
+    lib.mc_burn_opts_default(C.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    """Raw address of a torch tensor, numpy array or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Network:
+    """An uploaded network (handle owner). ``net`` is an object with the fields
+    of mc_inputs.Network (n_species, react, prod, A_f, ...)."""
+
+    def __init__(self, net):
+        self.src = net
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        self._keep = [np.ascontiguousarray(net.react, dtype=np.int32).ravel(),
+                      np.ascontiguousarray(net.prod, dtype=np.int32).ravel(),
+                      f(net.A_f), f(net.b_f), f(net.C_f), f(net.A_r), f(net.b_r), f(net.C_r), f(net.dE_eV)]
+        k = self._keep
+        d = mc_network_desc(net.n_species, net.n_elements, int(k[2].size), 1 if net.energy_eq else 0,
+                            k[0].ctypes.data_as(_ip), k[1].ctypes.data_as(_ip),
+                            *[a.ctypes.data_as(_dp) for a in k[2:]], float(net.gamma))
+        h = C.c_void_p()
+        check(lib.mc_network_create(C.byref(d), C.byref(h)), "mc_network_create")
+        self.handle = h
+        self.n_species = net.n_species
+        self.n_reactions = int(k[2].size)
+        self.energy_eq = bool(net.energy_eq)
+        self.n_ode = lib.mc_network_n_ode(h)
+
+    def close(self):
+        if self.handle:
+            lib.mc_network_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mc_network_create(net) -> Network:
+    return Network(net)
+
+
+def mc_network_destroy(net: Network) -> None:
+    net.close()
+
+
+def mc_burn_batch(net: Network, opts: mc_burn_opts | None, n_cells: int, dt: float, x, ld: int, T, ndens,
+                  rate_scale, status, stats, stream=None) -> int:
+    """Same arguments as the C function; arrays are torch tensors or numpy
+    arrays laid out as in mc.h ([rows][ld])."""
+    o = opts if opts is not None else mc_burn_opts_default()
+    return check(lib.mc_burn_batch(net.handle, C.byref(o), int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T),
+                                   _ptr(ndens), _ptr(rate_scale), _ptr(status), _ptr(stats),
+                                   _stream_ptr(stream)), "mc_burn_batch")
+
+
+def segment(net: Network, n_cells, ld, x, T, ndens, rate_scale, status, stats) -> mc_segment:
+    return mc_segment(net.handle.value, int(n_cells), int(ld), _ptr(x), _ptr(T), _ptr(ndens), _ptr(rate_scale),
+                      _ptr(status), _ptr(stats))
+
+
+def mc_burn_mixed(segs, opts: mc_burn_opts | None, dt: float, stream=None) -> int:
+    arr = (mc_segment * len(segs))(*segs)
+    o = opts if opts is not None else mc_burn_opts_default()
+    return check(lib.mc_burn_mixed(arr, len(segs), C.byref(o), float(dt), _stream_ptr(stream)), "mc_burn_mixed")
+
+
+class Graph:
+    def __init__(self, segs, opts, dt, totals=None, stream=None):
+        self._segs = (mc_segment * len(segs))(*segs)
+        self._opts = opts if opts is not None else mc_burn_opts_default()
+        h = C.c_void_p()
+        check(lib.mc_graph_create(self._segs, len(segs), C.byref(self._opts), float(dt), _ptr(totals),
+                                  _stream_ptr(stream), C.byref(h)), "mc_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        return check(lib.mc_graph_launch(self.handle, _stream_ptr(stream)), "mc_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib.mc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mc_graph_create(segs, opts, dt, totals=None, stream=None) -> Graph:
+    return Graph(segs, opts, dt, totals, stream)
+
+
+class Server:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 150 << 30, opts: mc_burn_opts | None = None):
+        self._opts = opts if opts is not None else mc_burn_opts_default()
+        h = C.c_void_p()
+        check(lib.mc_server_create(int(device), int(hbm_budget_bytes), C.byref(self._opts), C.byref(h)),
+              "mc_server_create")
+        self.handle = h
+
+    def submit(self, net: Network, n_cells, dt, x, ld, T, ndens, status) -> int:
+        rid = C.c_uint64()
+        check(lib.mc_request_submit(self.handle, net.handle, int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T),
+                                    _ptr(ndens), _ptr(status), C.byref(rid)), "mc_request_submit")
+        return rid.value
+
+    def poll(self, req_id: int):
+        info = mc_request_info()
+        rc = check(lib.mc_request_poll(self.handle, C.c_uint64(req_id), C.byref(info)), "mc_request_poll")
+        return rc, info
+
+    def drain(self, timeout_s: float = 600.0):
+        return check(lib.mc_server_drain(self.handle, float(timeout_s)), "mc_server_drain")
+
+    def close(self):
+        if self.handle:
+            check(lib.mc_server_destroy(self.handle), "mc_server_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mc_server_create(device=0, hbm_budget_bytes=150 << 30, opts=None) -> Server:
+    return Server(device, hbm_budget_bytes, opts)
+
+
+def mc_launch_count(reset: bool = False) -> int:
+    return int(lib.mc_launch_count(1 if reset else 0))

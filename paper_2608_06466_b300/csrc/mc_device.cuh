@@ -1,0 +1,710 @@
+// mc_device.cuh -- device side of the per-cell burn (sm_103a).
+//
+// One lane integrates one cell (thread-per-cell): the paper's single-zone
+// routine applied to every zone on the GPU (Software design section,
+// paragraph 3). The integrator is written as a per-lane state machine whose
+// loop body performs exactly ONE right-hand-side evaluation for every active
+// lane; what a lane does before and after it (Newton update, error test,
+// step/order change, a new cell) is cheap, so lanes of a warp stay converged
+// on the expensive part even when they sit in different cells, steps or
+// Newton iterations. That is what lets a persistent worker refill a lane the
+// moment its cell is done.
+//
+// Method (VODE-style BDF; the paper cites Brown, Byrne & Hindmarsh 1989 and
+// gives no details, so this is the library's restatement, shared with nothing
+// else in the tree):
+//   Nordsieck array z_j = h^j y^(j)/j!, j <= q <= 5, holding the polynomial
+//   through the last q+1 accepted values. Prediction is the Taylor shift
+//   z <- z*Pascal. The corrector e solves h f(z_0 + e) = z_1 + l_1 e by
+//   modified Newton with P = I - gamma J, gamma = h/l_1, where
+//   l = coeffs of prod_{j<=q} (1 + x/xi_j), xi_j = (t_n - t_{n-j})/h.
+//   Local error estimate e (1/xi_{q+1}) / l_1; step/order selection from the
+//   q-1, q, q+1 estimates; Jacobian kept 50 steps, matrix 20 steps or until
+//   gamma drifts 30 %.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mc {
+
+constexpr int QMAX = 5;
+constexpr double KB_EV = 8.617333262e-5;  // Boltzmann constant, eV/K
+
+// ---- policy constants of the integrator ------------------------------------
+constexpr int MAXCOR = 3;          // Newton corrections per attempt
+constexpr double RDIV = 2.0;       // divergence: del > RDIV * previous del
+constexpr double CRDOWN = 0.3;     // memory of the convergence rate
+constexpr double CORTES = 0.1;     // Newton error allowed, share of the local error
+constexpr double CRATE0 = 0.7;     // rate estimate after a new matrix
+constexpr double ETACF = 0.25;     // step factor after a Newton failure
+constexpr int MXNCF = 10;          // consecutive Newton failures allowed
+constexpr int KFC = 3;             // error failures before an order-1 restart
+constexpr double ETAMIN = 0.1;     // smallest factor after an error failure
+constexpr double BIAS_QM1 = 6.0, BIAS_Q = 6.0, BIAS_QP1 = 10.0, ADDON = 1.0e-6;
+constexpr double THRESH = 1.5;     // smallest growth worth a step change
+constexpr double ETAMX_FIRST = 1.0e4, ETAMX = 10.0;
+constexpr int MSBJ = 50;           // accepted steps between Jacobians
+constexpr int MSBP = 20;           // accepted steps between factorisations
+constexpr double CCMAX = 0.3;      // refactor when |gamma/gamma_P - 1| > CCMAX
+
+enum CellStatus : int { CELL_OK = 0, CELL_MAX_STEPS = 1, CELL_H_UNDERFLOW = 2, CELL_CONV_FAIL = 3,
+                        CELL_BAD_INPUT = 4, CELL_NONFINITE = 5 };
+enum Stat : int { ST_STEPS = 0, ST_ERR_FAILS, ST_CONV_FAILS, ST_RHS, ST_JAC, ST_LU, ST_NEWTON,
+                  ST_ORDER, NSTAT };
+
+// ---- network in device memory ----------------------------------------------
+struct __align__(64) RxPar {
+  double lnAf, bf, Cf;   // forward: k = exp(lnA + b ln T - C / T)
+  double lnAr, br, Cr;   // reverse
+  double dE;             // energy released by a forward event (eV)
+  double rev;            // 1 if the reverse direction exists
+};
+
+struct DNet {
+  int S, R, n, energy;   // species, reactions, ODEs, energy equation flag
+  double gm1;            // gamma - 1
+  const int4 *side;      // (reactant0, reactant1, product0, product1), -1 = empty
+  const RxPar *par;
+};
+
+// per-cell inputs the right-hand side needs
+struct CellIn {
+  double nd;             // total density n
+  double lnT, invT;      // isothermal networks: fixed temperature
+  const double *ks;      // rate_scale + cell (stride ks_ld) or nullptr
+  int64_t ks_ld;
+};
+
+// Right-hand side f(y). Returns false when the state cannot be evaluated (the
+// EOS gives T <= 0 or a non-finite value) or f is not finite.
+template <int N>
+__device__ __forceinline__ bool net_rhs(const DNet &net, const CellIn &c, const double *y,
+                                        double *f) {
+  const int S = net.S;
+  double lnT = c.lnT, invT = c.invT;
+  if (net.energy) {
+    double X = 0.0;
+    for (int i = 0; i < S; ++i) X += y[i];
+    const double T = net.gm1 * y[S] / (KB_EV * X);
+    if (!(T > 0.0) || !isfinite(T)) return false;
+    lnT = log(T);
+    invT = 1.0 / T;
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) f[i] = 0.0;
+  double fu = 0.0;
+  for (int r = 0; r < net.R; ++r) {
+    const int4 s = __ldg(&net.side[r]);
+    const RxPar &p = net.par[r];
+    const double lnAf = __ldg(&p.lnAf), bf = __ldg(&p.bf), Cf = __ldg(&p.Cf);
+    double kf = exp(lnAf + bf * lnT - Cf * invT);
+    double kr = 0.0;
+    if (__ldg(&p.rev) != 0.0) kr = exp(__ldg(&p.lnAr) + __ldg(&p.br) * lnT - __ldg(&p.Cr) * invT);
+    if (c.ks) {
+      const double sc = c.ks[r * c.ks_ld];
+      kf *= sc;
+      kr *= sc;
+    }
+    const double pf = (s.y < 0) ? y[s.x] : c.nd * y[s.x] * y[s.y];
+    const double pr = (s.w < 0) ? y[s.z] : c.nd * y[s.z] * y[s.w];
+    const double w = kf * pf - kr * pr;
+    f[s.x] -= w;
+    f[s.z] += w;
+    if (s.y >= 0) f[s.y] -= w;
+    if (s.w >= 0) f[s.w] += w;
+    if (net.energy) fu += __ldg(&p.dE) * w;
+  }
+  if (net.energy) f[S] = fu;
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < net.n && !isfinite(f[i])) ok = false;
+  return ok;
+}
+
+// Analytic Jacobian J[i*N + j] = d f_i / d y_j (row stride N), accumulated in
+// the matrix precision LT. For the energy form T depends on the state through
+// the EOS (dT/dx_j = -T / sum x, dT/du = (gamma-1) / (k_B sum x)); g_i =
+// d f_i / dT at fixed x enters every column through that chain rule.
+// dk/dT = k (b + C/T) / T.
+template <int N, typename LT>
+__device__ __forceinline__ bool net_jac(const DNet &net, const CellIn &c, const double *y, LT *J) {
+  const int S = net.S, n = net.n;
+  double lnT = c.lnT, invT = c.invT, T = 0.0, X = 0.0;
+  if (net.energy) {
+    for (int i = 0; i < S; ++i) X += y[i];
+    T = net.gm1 * y[S] / (KB_EV * X);
+    if (!(T > 0.0) || !isfinite(T)) return false;
+    lnT = log(T);
+    invT = 1.0 / T;
+  }
+  double g[N];
+  for (int i = 0; i < n * N; ++i) J[i] = (LT)0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) g[i] = 0.0;
+  for (int r = 0; r < net.R; ++r) {
+    const int4 s = __ldg(&net.side[r]);
+    const RxPar &p = net.par[r];
+    const double bf = __ldg(&p.bf), Cf = __ldg(&p.Cf);
+    double kf = exp(__ldg(&p.lnAf) + bf * lnT - Cf * invT);
+    double kr = 0.0, br = 0.0, Cr = 0.0;
+    if (__ldg(&p.rev) != 0.0) {
+      br = __ldg(&p.br);
+      Cr = __ldg(&p.Cr);
+      kr = exp(__ldg(&p.lnAr) + br * lnT - Cr * invT);
+    }
+    if (c.ks) {
+      const double sc = c.ks[r * c.ks_ld];
+      kf *= sc;
+      kr *= sc;
+    }
+    // column contributions d w / d x at fixed T, one per side slot
+    const int col[4] = {s.x, s.y, s.z, s.w};
+    double dw[4];
+    double pf, pr;
+    if (s.y < 0) { pf = y[s.x]; dw[0] = kf; dw[1] = 0.0; }
+    else { pf = c.nd * y[s.x] * y[s.y]; dw[0] = kf * (c.nd * y[s.y]); dw[1] = kf * (c.nd * y[s.x]); }
+    if (s.w < 0) { pr = y[s.z]; dw[2] = -kr; dw[3] = 0.0; }
+    else { pr = c.nd * y[s.z] * y[s.w]; dw[2] = -kr * (c.nd * y[s.w]); dw[3] = -kr * (c.nd * y[s.z]); }
+    const double dwdT = kf * (bf + Cf * invT) * invT * pf - kr * (br + Cr * invT) * invT * pr;
+    const double sgn[4] = {-1.0, -1.0, 1.0, 1.0};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (col[a] < 0) continue;
+      const int row = col[a];
+      g[row] += sgn[a] * dwdT;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (col[b] >= 0) J[row * N + col[b]] += (LT)(sgn[a] * dw[b]);
+    }
+    if (net.energy) {
+      const double dE = __ldg(&p.dE);
+      g[S] += dE * dwdT;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (col[b] >= 0) J[S * N + col[b]] += (LT)(dE * dw[b]);
+    }
+  }
+  if (net.energy) {
+    const double dTdx = -T / X, dTdu = net.gm1 / (KB_EV * X);
+    for (int i = 0; i < n; ++i) {
+      const LT gx = (LT)(g[i] * dTdx);
+      for (int j = 0; j < S; ++j) J[i * N + j] += gx;
+      J[i * N + S] += (LT)(g[i] * dTdu);
+    }
+  }
+  bool ok = true;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (!isfinite((double)J[i * N + j])) ok = false;
+  return ok;
+}
+
+// ---- dense LU with partial pivoting (first maximal |a| wins ties) ----------
+template <int N, typename LT>
+__device__ __forceinline__ bool lu_factor(int n, LT *a, unsigned char *piv) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    LT best = fabs(a[k * N + k]);
+    for (int i = k + 1; i < n; ++i) {
+      const LT v = fabs(a[i * N + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    piv[k] = (unsigned char)p;
+    if (best == (LT)0) return false;
+    if (p != k)
+      for (int j = 0; j < n; ++j) {
+        const LT tmp = a[k * N + j];
+        a[k * N + j] = a[p * N + j];
+        a[p * N + j] = tmp;
+      }
+    const LT inv = (LT)1 / a[k * N + k];
+    for (int i = k + 1; i < n; ++i) {
+      const LT m = a[i * N + k] * inv;
+      a[i * N + k] = m;
+      for (int j = k + 1; j < n; ++j) a[i * N + j] -= m * a[k * N + j];
+    }
+  }
+  return true;
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void lu_solve(int n, const LT *a, const unsigned char *piv, double *bd) {
+  LT b[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) b[i] = (i < n) ? (LT)bd[i] : (LT)0;
+  for (int k = 0; k < n; ++k) {
+    const int p = piv[k];
+    if (p != k) {
+      const LT tmp = b[k];
+      b[k] = b[p];
+      b[p] = tmp;
+    }
+  }
+  for (int i = 1; i < n; ++i) {
+    LT s = b[i];
+    for (int j = 0; j < i; ++j) s -= a[i * N + j] * b[j];
+    b[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    LT s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= a[i * N + j] * b[j];
+    b[i] = s / a[i * N + i];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) bd[i] = (double)b[i];
+}
+
+// ---- integrator state of one lane -------------------------------------------
+enum Phase : int { PH_IDLE = 0, PH_F0, PH_HW, PH_NEWTON, PH_RESTART, PH_DONE };
+
+struct Opts {
+  double rtol, atol;
+  int qmax, max_steps;
+};
+
+template <int N, typename LT>
+struct Lane {
+  double z[QMAX + 2][N];   // Nordsieck array (column q+1 used during an order rise)
+  double e[N];             // accumulated correction
+  double es[N];            // correction saved for the order-rise estimate
+  double iw[N];            // 1 / error weight, from the start of the step
+  double y[N];             // point at which f is wanted next
+  double f[N];             // f(y)
+  LT J[N * N];             // Jacobian, kept between evaluations
+  LT P[N * N];             // factored iteration matrix
+  unsigned char piv[N];
+  double l[QMAX + 1];
+  double hist[QMAX + 3];   // accepted step sizes, most recent first
+  double t, h, tend, crate, gamma_p, gamma, cq, esave_h, delp, eta_max, h0;
+  CellIn cin;
+  int64_t cell;
+  int q, qwait, nef, ncf, jage, page, attempts, m, phase, status;
+  bool need_j, need_p, jcur, have_es, last;
+  int st[NSTAT];
+};
+
+template <int N>
+__device__ __forceinline__ double wrms(int n, const double *v, const double *iw) {
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) {
+      const double r = v[i] * iw[i];
+      s += r * r;
+    }
+  return sqrt(s / n);
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void rescale(Lane<N, LT> &L, int n, double eta) {
+  double r = 1.0;
+  for (int j = 1; j <= L.q; ++j) {
+    r *= eta;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.z[j][i] *= r;
+  }
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void predict(Lane<N, LT> &L, int n) {
+  const int q = L.q;
+  for (int k = 0; k < q; ++k)
+    for (int j = q; j > k; --j)
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) L.z[j - 1][i] += L.z[j][i];
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void retract(Lane<N, LT> &L, int n) {
+  const int q = L.q;
+  for (int k = q - 1; k >= 0; --k)
+    for (int j = k + 1; j <= q; ++j)
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) L.z[j - 1][i] -= L.z[j][i];
+}
+
+// xi_j = (sum of the first j gaps)/h for j = 1..m
+__device__ __forceinline__ void xi_of(double h, const double *gaps, int m, double *xi) {
+  double s = 0.0;
+  for (int j = 0; j < m; ++j) {
+    s += gaps[j];
+    xi[j] = s / h;
+  }
+}
+
+// coefficients of x * prod_{i<k}(x + xi_i), k = number of factors (c[0..k])
+__device__ __forceinline__ void shifted_product(int k, const double *xi, double *c) {
+  for (int j = 0; j <= k; ++j) c[j] = 0.0;
+  c[1] = 1.0;
+  for (int i = 1; i <= k - 1; ++i) {
+    const double a = xi[i - 1];
+    for (int j = i + 1; j >= 1; --j) c[j] = c[j - 1] + a * c[j];
+    c[0] = a * c[0];
+  }
+}
+
+__device__ __forceinline__ double harmonic(int k) {
+  double s = 0.0;
+  for (int j = 1; j <= k; ++j) s += 1.0 / j;
+  return s;
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void finish(Lane<N, LT> &L, int status) {
+  L.status = status;
+  L.phase = PH_DONE;
+}
+
+// Start a step attempt (or finish the cell): clip the last step to t_end,
+// weights from the accepted state, predict, variable-step coefficients.
+template <int N, typename LT>
+__device__ void begin_step(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+  const int n = net.n;
+  if (!(L.t < L.tend)) { finish(L, CELL_OK); return; }
+  if (L.attempts >= o.max_steps) { finish(L, CELL_MAX_STEPS); return; }
+  L.last = false;
+  if (L.t + L.h >= L.tend) {
+    const double hn = L.tend - L.t;
+    rescale(L, n, hn / L.h);
+    L.h = hn;
+    L.last = true;
+  }
+  L.attempts += 1;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) L.iw[i] = 1.0 / (o.rtol * fabs(L.z[0][i]) + o.atol);
+  predict(L, n);
+  const int q = L.q;
+  double gaps[QMAX + 2], xi[QMAX + 2];
+  gaps[0] = L.h;
+  for (int k = 0; k < q; ++k) gaps[k + 1] = L.hist[k];
+  xi_of(L.h, gaps, q + 1, xi);
+  // l = coefficients of prod_{j<=q} (1 + x/xi_j)
+  for (int k = 0; k <= q; ++k) L.l[k] = 0.0;
+  L.l[0] = 1.0;
+  for (int j = 1; j <= q; ++j) {
+    const double c = 1.0 / xi[j - 1];
+    for (int k = j; k >= 1; --k) L.l[k] += c * L.l[k - 1];
+  }
+  L.cq = (1.0 / xi[q]) / L.l[1];
+  L.gamma = L.h / L.l[1];
+  L.jcur = false;
+  L.m = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) {
+      L.e[i] = 0.0;
+      L.y[i] = L.z[0][i];
+    }
+  L.phase = PH_NEWTON;
+}
+
+template <int N, typename LT>
+__device__ void conv_failure(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+  const int n = net.n;
+  retract(L, n);
+  L.ncf += 1;
+  L.st[ST_CONV_FAILS] += 1;
+  if (L.ncf >= MXNCF) { finish(L, CELL_CONV_FAIL); return; }
+  rescale(L, n, ETACF);
+  L.h *= ETACF;
+  L.need_p = true;
+  L.qwait = L.q + 1;
+  L.have_es = false;
+  if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
+  begin_step(L, net, o);
+}
+
+// Order change helper: drop q -> q-1 (z_j -= c_j z_q) with xi at the array's point.
+template <int N, typename LT>
+__device__ __forceinline__ void lower_order(Lane<N, LT> &L, int n, const double *xi) {
+  double c[QMAX + 2];
+  const int q = L.q;
+  shifted_product(q, xi, c);
+  for (int j = 1; j < q; ++j)
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.z[j][i] -= c[j] * L.z[q][i];
+  L.q = q - 1;
+}
+
+template <int N, typename LT>
+__device__ void after_convergence(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+  const int n = net.n;
+  const int q = L.q;
+  const double dsm = L.cq * wrms<N>(n, L.e, L.iw);
+  double xi[QMAX + 2];
+  if (dsm > 1.0) {
+    // ---- error test failed
+    retract(L, n);
+    L.nef += 1;
+    L.st[ST_ERR_FAILS] += 1;
+    L.have_es = false;
+    if (L.nef >= KFC) {
+      // restart at order 1 from the accepted state: needs f(z_0)
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) L.y[i] = L.z[0][i];
+      L.phase = PH_RESTART;
+      return;
+    }
+    double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
+    int qn = q;
+    if (q > 1) {
+      xi_of(L.h, L.hist, q, xi);
+      double prod = 1.0, l1 = 0.0;
+      for (int j = 1; j <= q - 1; ++j) {
+        prod *= xi[j - 1];
+        l1 += 1.0 / xi[j - 1];
+      }
+      const double est = (prod / l1) * wrms<N>(n, L.z[q], L.iw);
+      const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
+      if (eta_m > eta) { eta = eta_m; qn = q - 1; }
+    }
+    eta = fmax(ETAMIN, fmin(eta, 1.0));
+    if (qn < q) lower_order(L, n, xi);
+    rescale(L, n, eta);
+    L.h *= eta;
+    L.qwait = L.q + 1;
+    if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
+    begin_step(L, net, o);
+    return;
+  }
+  // ---- accept
+  for (int j = 0; j <= q; ++j)
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.z[j][i] += L.l[j] * L.e[i];
+  L.t = L.last ? L.tend : L.t + L.h;
+  for (int k = QMAX + 2; k > 0; --k) L.hist[k] = L.hist[k - 1];
+  L.hist[0] = L.h;
+  L.st[ST_STEPS] += 1;
+  L.nef = 0;
+  L.ncf = 0;
+  L.jage += 1;
+  L.page += 1;
+  L.qwait -= 1;
+  if (L.qwait == 1 && q < o.qmax) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.es[i] = L.e[i];
+    L.esave_h = L.h;
+    L.have_es = true;
+  }
+  if (L.last) { finish(L, CELL_OK); return; }
+  if (L.qwait > 0) { begin_step(L, net, o); return; }
+  // ---- step size and order selection
+  double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
+  int qn = q;
+  xi_of(L.h, L.hist, q + 1, xi);
+  if (q > 1) {
+    double prod = 1.0, l1 = 0.0;
+    for (int j = 1; j <= q - 1; ++j) {
+      prod *= xi[j - 1];
+      l1 += 1.0 / xi[j - 1];
+    }
+    const double est = (prod / l1) * wrms<N>(n, L.z[q], L.iw);
+    const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
+    if (eta_m > eta) { eta = eta_m; qn = q - 1; }
+  }
+  if (q < o.qmax && L.have_es) {
+    const double r = pow(L.h / L.esave_h, (double)(q + 1));
+    double dv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) dv[i] = (i < n) ? L.e[i] - r * L.es[i] : 0.0;
+    const double est = wrms<N>(n, dv, L.iw) / ((double)(q + 2) * harmonic(q + 1));
+    const double eta_p = 1.0 / (pow(BIAS_QP1 * est, 1.0 / (q + 2)) + ADDON);
+    if (eta_p > eta) { eta = eta_p; qn = q + 1; }
+  }
+  L.have_es = false;
+  if (eta < THRESH) {
+    L.qwait = 2;
+    begin_step(L, net, o);
+    return;
+  }
+  eta = fmin(eta, L.eta_max);
+  L.eta_max = ETAMX;
+  if (qn > q) {
+    double prod = 1.0, c[QMAX + 2];
+    for (int j = 1; j <= q + 1; ++j) prod *= xi[j - 1];
+    const double C = 1.0 / prod;
+    shifted_product(q + 1, xi, c);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.z[q + 1][i] = 0.0;
+    for (int j = 1; j <= q + 1; ++j)
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) L.z[j][i] += c[j] * C * L.e[i];
+    L.q = q + 1;
+  } else if (qn < q) {
+    lower_order(L, n, xi);
+  }
+  rescale(L, n, eta);
+  L.h *= eta;
+  L.qwait = L.q + 1;
+  begin_step(L, net, o);
+}
+
+// One modified-Newton correction with f = f(y) just evaluated.
+// 0 = continue, 1 = converged, 2 = failed, 3 = failed (could not evaluate)
+template <int N, typename LT>
+__device__ int newton_iter(Lane<N, LT> &L, const DNet &net, bool ok) {
+  const int n = net.n;
+  if (!ok) return 3;
+  L.st[ST_RHS] += 1;
+  if (L.m == 0) {
+    bool newp = false;
+    if (L.need_j || L.jage >= MSBJ) {
+      if (!net_jac<N, LT>(net, L.cin, L.y, L.J)) return 3;
+      L.st[ST_JAC] += 1;
+      L.jcur = true;
+      L.need_j = false;
+      L.jage = 0;
+      newp = true;
+    }
+    if (newp || L.need_p || L.page >= MSBP || fabs(L.gamma / L.gamma_p - 1.0) > CCMAX) {
+      const LT g = (LT)L.gamma;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          L.P[i * N + j] = (i == j ? (LT)1 : (LT)0) - g * L.J[i * N + j];
+      L.st[ST_LU] += 1;
+      L.gamma_p = L.gamma;
+      L.page = 0;
+      L.need_p = false;
+      L.crate = CRATE0;
+      if (!lu_factor<N, LT>(n, L.P, L.piv)) {
+        L.need_p = true;
+        return 2;
+      }
+    }
+  }
+  double d[N];
+  const double rl1 = L.l[1];
+#pragma unroll
+  for (int i = 0; i < N; ++i) d[i] = (i < n) ? (L.h * L.f[i] - L.z[1][i]) / rl1 - L.e[i] : 0.0;
+  lu_solve<N, LT>(n, L.P, L.piv, d);
+  L.st[ST_NEWTON] += 1;
+  if (L.gamma != L.gamma_p) {
+    const double sc = 2.0 / (1.0 + L.gamma / L.gamma_p);
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] *= sc;
+  }
+  const double del = wrms<N>(n, d, L.iw);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) {
+      L.e[i] += d[i];
+      L.y[i] = L.z[0][i] + L.e[i];
+    }
+  if (L.m > 0) L.crate = fmax(CRDOWN * L.crate, del / L.delp);
+  const double dcon = del * fmin(1.0, L.crate) * L.cq / CORTES;
+  if (dcon <= 1.0) return 1;
+  L.m += 1;
+  if (L.m == MAXCOR || (L.m >= 2 && del > RDIV * L.delp)) return 2;
+  L.delp = del;
+  return 0;
+}
+
+// Consume f(y) according to the lane's phase and prepare the next y.
+template <int N, typename LT>
+__device__ void advance(Lane<N, LT> &L, const DNet &net, const Opts &o, bool ok) {
+  const int n = net.n;
+  switch (L.phase) {
+    case PH_F0: {
+      if (!ok) { finish(L, CELL_BAD_INPUT); return; }
+      L.st[ST_RHS] += 1;
+      // starting step (Hairer, Norsett & Wanner, Solving ODEs I, II.4), p = 1
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) L.iw[i] = 1.0 / (o.rtol * fabs(L.z[0][i]) + o.atol);
+      const double d0 = wrms<N>(n, L.z[0], L.iw), d1 = wrms<N>(n, L.f, L.iw);
+      double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+      h0 = fmin(h0, L.tend);
+      L.h0 = h0;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) {
+          L.e[i] = L.f[i];  // f0 parked in e
+          L.y[i] = L.z[0][i] + h0 * L.f[i];
+        }
+      L.st[ST_RHS] += 1;
+      L.phase = PH_HW;
+      return;
+    }
+    case PH_HW: {
+      double h = L.h0;
+      if (ok) {
+        double dv[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) dv[i] = (i < n) ? L.f[i] - L.e[i] : 0.0;
+        const double d1 = wrms<N>(n, L.e, L.iw);
+        const double d2 = wrms<N>(n, dv, L.iw) / L.h0;
+        const double dm = fmax(d1, d2);
+        const double h1 = (dm <= 1e-15) ? fmax(1e-6, L.h0 * 1e-3) : sqrt(0.01 / dm);
+        h = fmin(fmin(100.0 * L.h0, h1), L.tend);
+      }
+      L.h = h;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) L.z[1][i] = h * L.e[i];
+      L.t = 0.0;
+      L.q = 1;
+      L.qwait = 2;
+      for (int k = 0; k < QMAX + 3; ++k) L.hist[k] = h;
+      L.need_j = true;
+      L.need_p = true;
+      L.crate = CRATE0;
+      L.gamma_p = 1.0;
+      L.eta_max = ETAMX_FIRST;
+      L.nef = L.ncf = 0;
+      L.jage = L.page = 0;
+      L.have_es = false;
+      L.attempts = 0;
+      begin_step(L, net, o);
+      return;
+    }
+    case PH_NEWTON: {
+      const int r = newton_iter<N, LT>(L, net, ok);
+      if (r == 0) return;
+      if (r == 1) { after_convergence(L, net, o); return; }
+      if (r == 2 && !L.jcur) {
+        // stale Jacobian: refresh it and redo the corrector from the prediction
+        L.need_j = true;
+        L.m = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+          if (i < n) {
+            L.e[i] = 0.0;
+            L.y[i] = L.z[0][i];
+          }
+        return;
+      }
+      conv_failure(L, net, o);
+      return;
+    }
+    case PH_RESTART: {
+      if (!ok) { finish(L, CELL_NONFINITE); return; }
+      L.st[ST_RHS] += 1;
+      L.h *= ETAMIN;
+      L.q = 1;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) L.z[1][i] = L.h * L.f[i];
+      L.qwait = 2;
+      if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
+      begin_step(L, net, o);
+      return;
+    }
+    default:
+      return;
+  }
+}
+
+}  // namespace mc

@@ -1,0 +1,9 @@
+// mc_inst_40.cu -- burn kernels for networks of up to 40 ODEs.
+#include "mc_launch.cuh"
+
+namespace mc {
+template mc_status launch_one<40, double>(const DNet &, const Opts &, const CellArgs &, int, int, int,
+                                          unsigned long long *, cudaStream_t);
+template mc_status launch_one<40, float>(const DNet &, const Opts &, const CellArgs &, int, int, int,
+                                         unsigned long long *, cudaStream_t);
+}  // namespace mc

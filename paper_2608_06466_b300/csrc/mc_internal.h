@@ -1,0 +1,55 @@
+// mc_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "mc.h"
+#include "mc_device.cuh"
+
+namespace mc {
+struct CellArgs;
+}
+
+struct mc_network {
+  int S = 0, R = 0, n = 0, energy = 0, device = 0;
+  double gamma = 5.0 / 3.0;
+  std::vector<int4> side_h;
+  std::vector<mc::RxPar> par_h;
+  void *side_d = nullptr;
+  void *par_d = nullptr;
+};
+
+namespace mc {
+
+constexpr int NMAX_ODE = 40;      // largest ODE count compiled
+constexpr int RMAX_REACT = 512;   // largest reaction count accepted
+constexpr int MAX_QUEUES = 16;    // persistent queue counters per device
+
+mc_status set_error(mc_status code, const char *fmt, ...);
+mc_status cuda_error(cudaError_t e, const char *what);
+void count_launch(int64_t k);
+DNet dnet_of(const mc_network *net);
+mc_status check_opts(const mc_burn_opts *in, mc_burn_opts *out);
+mc_status scratch_get(int dev, int64_t retry_cells, unsigned long long **next, uint32_t **rcount,
+                      int32_t **retry);
+mc_status burn_device(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st);
+
+// launch shape chosen for a network and options
+struct Tuned {
+  int variant;        // MC_VARIANT_PLAIN or MC_VARIANT_PERSISTENT
+  int threads;        // threads per block
+  int blocks_per_sm;  // persistent grid size per SM
+};
+Tuned autotune_pick(const mc_network *net, const mc_burn_opts &o);
+
+// Launch the burn kernel of ODE-count bucket N (network n <= N) with matrix
+// precision LT; defined in mc_launch.cuh, instantiated in mc_inst_<N>.cu.
+template <int N, typename LT>
+mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int variant, int threads,
+                     int blocks_per_sm, unsigned long long *next, cudaStream_t st);
+
+}  // namespace mc

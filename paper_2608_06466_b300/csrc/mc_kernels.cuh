@@ -1,0 +1,168 @@
+// mc_kernels.cuh -- burn kernels: plain (one launch, one thread per cell) and
+// persistent (workers pull cells from a queue; a lane whose cell is done takes
+// the next one, so a warp never idles behind one stiff cell -- the thread
+// divergence the paper's Software design section, paragraph 3, names).
+#pragma once
+
+#include "mc_device.cuh"
+
+namespace mc {
+
+// Cell arrays of one launch (structure-of-arrays, see mc.h).
+struct CellArgs {
+  int64_t n_cells;          // number of cells (or entries of index)
+  int64_t ld;
+  double dt;
+  double *x;
+  double *T;
+  const double *nd;
+  const double *ks;
+  int32_t *status;
+  int32_t *stats;
+  const int32_t *index;     // optional cell list: entry k is cell index[k]
+  const uint32_t *n_dev;    // optional device-side count overriding n_cells
+  int32_t *retry;           // FP32 pass: cells to redo in FP64 (nullptr = none)
+  uint32_t *retry_count;
+};
+
+__device__ __forceinline__ int64_t cell_of(const CellArgs &a, int64_t k) {
+  return a.index ? (int64_t)a.index[k] : k;
+}
+
+__device__ __forceinline__ int64_t count_of(const CellArgs &a) {
+  return a.n_dev ? (int64_t)(*a.n_dev) : a.n_cells;
+}
+
+// Load cell c: inputs checked the way the burn's definition needs them
+// (finite abundances, T > 0, n > 0; for the energy form sum x > 0), the
+// energy form's u = (sum x) k_B T / (gamma - 1). Sets PH_F0, or PH_DONE with
+// CELL_BAD_INPUT (outputs then left untouched).
+template <int N, typename LT>
+__device__ void load_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a, int64_t c) {
+  const int S = net.S, n = net.n;
+  L.cell = c;
+  L.status = CELL_OK;
+  L.q = 0;
+#pragma unroll
+  for (int k = 0; k < NSTAT; ++k) L.st[k] = 0;
+  bool good = true;
+  double X = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double v = (i < S) ? a.x[i * a.ld + c] : 0.0;
+    L.z[0][i] = v;
+    if (i < S) {
+      X += v;
+      if (!isfinite(v)) good = false;
+    }
+  }
+  const double nd = a.nd ? a.nd[c] : 1.0;
+  if (!(nd > 0.0) || !isfinite(nd)) good = false;
+  const double T = a.T ? a.T[c] : 1.0;
+  if (!(T > 0.0) || !isfinite(T)) good = false;
+  L.cin.nd = nd;
+  L.cin.ks = a.ks ? a.ks + c : nullptr;
+  L.cin.ks_ld = a.ld;
+  if (net.energy) {
+    if (!(X > 0.0) || !isfinite(X)) good = false;
+    L.z[0][S] = X * KB_EV * T / net.gm1;
+    L.cin.lnT = 0.0;
+    L.cin.invT = 0.0;
+  } else {
+    L.cin.lnT = log(T);
+    L.cin.invT = 1.0 / T;
+  }
+  if (!good) {
+    L.status = CELL_BAD_INPUT;
+    L.phase = PH_DONE;
+    L.m = -1;  // marks "inputs rejected": outputs are not written
+    return;
+  }
+  L.m = 0;
+  L.tend = a.dt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) L.y[i] = (i < n) ? L.z[0][i] : 0.0;
+  L.phase = PH_F0;
+}
+
+// Write cell results. FP32-matrix runs hand Newton and step-size failures to
+// an FP64 retry list instead of writing them (the inputs stay in place).
+template <int N, typename LT>
+__device__ void store_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a) {
+  const int64_t c = L.cell;
+  const int S = net.S;
+  if (a.retry && (L.status == CELL_CONV_FAIL || L.status == CELL_H_UNDERFLOW)) {
+    const uint32_t k = atomicAdd(a.retry_count, 1u);
+    a.retry[k] = (int32_t)c;
+    return;
+  }
+  const bool rejected = (L.status == CELL_BAD_INPUT && L.m < 0);
+  if (!rejected) {
+    double X = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < S) {
+        a.x[i * a.ld + c] = L.z[0][i];
+        X += L.z[0][i];
+      }
+    if (net.energy) a.T[c] = net.gm1 * L.z[0][S] / (KB_EV * X);
+  }
+  a.status[c] = L.status;
+  if (a.stats) {
+    L.st[ST_ORDER] = (L.status == CELL_BAD_INPUT) ? 0 : L.q;
+#pragma unroll
+    for (int k = 0; k < NSTAT; ++k) a.stats[k * a.ld + c] = L.st[k];
+  }
+}
+
+template <int N, typename LT>
+__global__ void __launch_bounds__(128) k_burn_plain(DNet net, Opts o, CellArgs a) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count_of(a)) return;
+  Lane<N, LT> L;
+  load_cell(L, net, a, cell_of(a, k));
+  while (L.phase != PH_DONE) {
+    const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
+    advance(L, net, o, ok);
+  }
+  store_cell(L, net, a);
+}
+
+// Persistent worker. `next` counts cells handed out (reset to 0 before the
+// launch). Every lane of every warp runs the loop, so warp-wide votes are safe.
+template <int N, typename LT>
+__global__ void __launch_bounds__(128) k_burn_persistent(DNet net, Opts o, CellArgs a,
+                                                         unsigned long long *next) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = count_of(a);
+  Lane<N, LT> L;
+  L.phase = PH_IDLE;
+  bool active = true;
+  for (;;) {
+    if (L.phase == PH_DONE) {
+      store_cell(L, net, a);
+      L.phase = PH_IDLE;
+    }
+    const bool want = (L.phase == PH_IDLE) && active;
+    const unsigned need = __ballot_sync(FULL, want);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(need));
+      base = __shfl_sync(FULL, base, leader);
+      if (want) {
+        const int64_t k = (int64_t)base + __popc(need & ((1u << lane) - 1u));
+        if (k < total) load_cell(L, net, a, cell_of(a, k));
+        else active = false;
+      }
+    }
+    if (!__any_sync(FULL, L.phase != PH_IDLE)) break;
+    if (L.phase != PH_IDLE && L.phase != PH_DONE) {
+      const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
+      advance(L, net, o, ok);
+    }
+  }
+}
+
+}  // namespace mc

@@ -1,0 +1,340 @@
+// mc_lib.cu -- C ABI of the per-cell burn (see include/mc.h): network upload,
+// batch burns (plain / persistent, FP64 / FP32 iteration matrix with an FP64
+// retry pass), host-pointer staging, error reporting.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mc.h"
+#include "mc_kernels.cuh"
+#include "mc_internal.h"
+
+using namespace mc;
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+static thread_local int64_t g_launches = 0;
+
+mc_status mc::set_error(mc_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+mc_status mc::cuda_error(cudaError_t e, const char *what) {
+  return set_error(MC_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void mc::count_launch(int64_t k) { g_launches += k; }
+
+extern "C" const char *mc_last_error(void) { return g_err.c_str(); }
+extern "C" int32_t mc_version(void) { return 1; }
+extern "C" int64_t mc_launch_count(int32_t reset) {
+  const int64_t v = g_launches;
+  if (reset) g_launches = 0;
+  return v;
+}
+
+extern "C" void mc_burn_opts_default(mc_burn_opts *o) {
+  if (!o) return;
+  o->rtol = 1e-6;
+  o->atol = 1e-10;
+  o->max_order = 5;
+  o->max_steps = 100000;
+  o->lu_precision = 64;
+  o->variant = MC_VARIANT_AUTO;
+  o->block_threads = 0;
+  o->blocks_per_sm = 0;
+}
+
+// ---------------------------------------------------------------- networks
+extern "C" mc_status mc_network_create(const mc_network_desc *d, mc_network **out) {
+  if (!d || !out) return set_error(MC_E_INVALID, "mc_network_create: null argument");
+  *out = nullptr;
+  const int S = d->n_species, R = d->n_reactions;
+  const int n = S + (d->energy_eq ? 1 : 0);
+  if (S < 1 || R < 0 || (R > 0 && (!d->react || !d->prod || !d->A_f || !d->b_f || !d->C_f ||
+                                   !d->A_r || !d->b_r || !d->C_r || !d->dE_eV)))
+    return set_error(MC_E_INVALID, "mc_network_create: bad sizes or null arrays");
+  if (n > NMAX_ODE || R > RMAX_REACT)
+    return set_error(MC_E_UNSUPPORTED, "mc_network_create: %d ODEs / %d reactions exceed %d / %d", n,
+                     R, NMAX_ODE, RMAX_REACT);
+  if (d->energy_eq && !(d->gamma > 1.0) )
+    return set_error(MC_E_INVALID, "mc_network_create: gamma must exceed 1");
+  std::vector<int4> side(R > 0 ? R : 1);
+  std::vector<RxPar> par(R > 0 ? R : 1);
+  for (int r = 0; r < R; ++r) {
+    int v[4] = {d->react[2 * r], d->react[2 * r + 1], d->prod[2 * r], d->prod[2 * r + 1]};
+    for (int k = 0; k < 4; ++k)
+      if (v[k] < -1 || v[k] >= S) return set_error(MC_E_INVALID, "reaction %d: species index out of range", r);
+    if (v[0] < 0 || v[2] < 0) return set_error(MC_E_INVALID, "reaction %d: slot 0 of a side is empty", r);
+    side[r] = make_int4(v[0], v[1], v[2], v[3]);
+    const double Af = d->A_f[r], Ar = d->A_r[r];
+    if (!(Af >= 0.0) || !(Ar >= 0.0) || !std::isfinite(Af) || !std::isfinite(Ar) ||
+        !std::isfinite(d->b_f[r]) || !std::isfinite(d->C_f[r]) || !std::isfinite(d->b_r[r]) ||
+        !std::isfinite(d->C_r[r]) || !std::isfinite(d->dE_eV[r]))
+      return set_error(MC_E_INVALID, "reaction %d: rate parameters must be finite, A >= 0", r);
+    par[r].lnAf = Af > 0.0 ? std::log(Af) : -INFINITY;
+    par[r].bf = d->b_f[r];
+    par[r].Cf = d->C_f[r];
+    par[r].lnAr = Ar > 0.0 ? std::log(Ar) : -INFINITY;
+    par[r].br = d->b_r[r];
+    par[r].Cr = d->C_r[r];
+    par[r].dE = d->dE_eV[r];
+    par[r].rev = Ar > 0.0 ? 1.0 : 0.0;
+  }
+  mc_network *net = new (std::nothrow) mc_network();
+  if (!net) return set_error(MC_E_NOMEM, "mc_network_create: host allocation");
+  net->S = S;
+  net->R = R;
+  net->n = n;
+  net->energy = d->energy_eq ? 1 : 0;
+  net->gamma = d->gamma;
+  net->side_h = side;
+  net->par_h = par;
+  cudaError_t e = cudaGetDevice(&net->device);
+  if (e != cudaSuccess) { delete net; return cuda_error(e, "cudaGetDevice"); }
+  e = cudaMalloc(&net->side_d, sizeof(int4) * side.size());
+  if (e == cudaSuccess) e = cudaMalloc(&net->par_d, sizeof(RxPar) * par.size());
+  if (e == cudaSuccess) e = cudaMemcpy(net->side_d, side.data(), sizeof(int4) * side.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(net->par_d, par.data(), sizeof(RxPar) * par.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(net->side_d);
+    cudaFree(net->par_d);
+    delete net;
+    return cuda_error(e, "mc_network_create upload");
+  }
+  *out = net;
+  return MC_OK;
+}
+
+extern "C" mc_status mc_network_destroy(mc_network *net) {
+  if (!net) return MC_OK;
+  cudaFree(net->side_d);
+  cudaFree(net->par_d);
+  delete net;
+  return MC_OK;
+}
+
+extern "C" int32_t mc_network_n_ode(const mc_network *net) { return net ? net->n : 0; }
+
+DNet mc::dnet_of(const mc_network *net) {
+  DNet d;
+  d.S = net->S;
+  d.R = net->R;
+  d.n = net->n;
+  d.energy = net->energy;
+  d.gm1 = net->gamma - 1.0;
+  d.side = (const int4 *)net->side_d;
+  d.par = (const RxPar *)net->par_d;
+  return d;
+}
+
+// ---------------------------------------------------------------- device scratch
+// Library-owned scratch per device: the persistent queue counter and the
+// FP32 pass's retry list (grown on demand, never shrunk).
+namespace {
+struct DevScratch {
+  unsigned long long *next = nullptr;   // [MAX_QUEUES]
+  uint32_t *retry_count = nullptr;
+  int32_t *retry = nullptr;
+  int64_t retry_cap = 0;
+};
+std::mutex g_scratch_mu;
+DevScratch g_scratch[64];
+}  // namespace
+
+mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **next, uint32_t **rcount,
+                          int32_t **retry) {
+  if (dev < 0 || dev >= 64) return set_error(MC_E_INVALID, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  DevScratch &s = g_scratch[dev];
+  cudaError_t e;
+  if (!s.next) {
+    e = cudaMalloc(&s.next, sizeof(unsigned long long) * MAX_QUEUES + sizeof(uint32_t) * 4);
+    if (e != cudaSuccess) return cuda_error(e, "scratch allocation");
+    s.retry_count = (uint32_t *)(s.next + MAX_QUEUES);
+  }
+  if (retry_cells > s.retry_cap) {
+    // the old list may still be read by work queued on another stream
+    if (s.retry) {
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_error(e, "scratch grow sync");
+      cudaFree(s.retry);
+      s.retry = nullptr;
+      s.retry_cap = 0;
+    }
+    e = cudaMalloc(&s.retry, sizeof(int32_t) * retry_cells);
+    if (e != cudaSuccess) return cuda_error(e, "retry list allocation");
+    s.retry_cap = retry_cells;
+  }
+  *next = s.next;
+  *rcount = s.retry_count;
+  *retry = s.retry;
+  return MC_OK;
+}
+
+// ---------------------------------------------------------------- launches
+namespace {
+
+template <typename LT>
+mc_status dispatch(const mc_network *net, const DNet &d, const Opts &o, const CellArgs &a,
+                   int variant, int threads, int bps, unsigned long long *next, cudaStream_t st) {
+  switch (net->n) {
+    case 3: return launch_one<3, LT>(d, o, a, variant, threads, bps, next, st);
+    case 13: return launch_one<13, LT>(d, o, a, variant, threads, bps, next, st);
+    case 33: return launch_one<33, LT>(d, o, a, variant, threads, bps, next, st);
+    default: break;
+  }
+  if (net->n <= 8) return launch_one<8, LT>(d, o, a, variant, threads, bps, next, st);
+  if (net->n <= 16) return launch_one<16, LT>(d, o, a, variant, threads, bps, next, st);
+  if (net->n <= 24) return launch_one<24, LT>(d, o, a, variant, threads, bps, next, st);
+  return launch_one<NMAX_ODE, LT>(d, o, a, variant, threads, bps, next, st);
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return true;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+mc_status mc::check_opts(const mc_burn_opts *opts, mc_burn_opts *o) {
+  mc_burn_opts_default(o);
+  if (opts) *o = *opts;
+  if (!(o->rtol > 0.0) || !(o->atol > 0.0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol))
+    return set_error(MC_E_INVALID, "rtol and atol must be positive and finite");
+  if (o->max_order < 1 || o->max_order > QMAX) return set_error(MC_E_INVALID, "max_order must be 1..5");
+  if (o->max_steps < 1) return set_error(MC_E_INVALID, "max_steps must be positive");
+  if (o->lu_precision != 64 && o->lu_precision != 32)
+    return set_error(MC_E_INVALID, "lu_precision must be 64 or 32");
+  if (o->variant < 0 || o->variant > MC_VARIANT_PERSISTENT) return set_error(MC_E_INVALID, "unknown variant");
+  if (o->block_threads < 0 || o->block_threads > 1024 || (o->block_threads % 32) != 0)
+    return set_error(MC_E_INVALID, "block_threads must be a multiple of 32 up to 1024");
+  if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) return set_error(MC_E_INVALID, "blocks_per_sm must be 0..32");
+  return MC_OK;
+}
+
+// Burn one segment on the device (device pointers). Runs the FP32 pass and,
+// when it leaves Newton failures behind, the FP64 retry pass over them.
+mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const CellArgs &a0,
+                          cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  Tuned tu = autotune_pick(net, ob);
+  Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps};
+  const DNet d = dnet_of(net);
+  unsigned long long *next;
+  uint32_t *rcount;
+  int32_t *retry;
+  mc_status s = scratch_get(dev, ob.lu_precision == 32 ? a0.n_cells : 0, &next, &rcount, &retry);
+  if (s != MC_OK) return s;
+  if (ob.lu_precision == 64)
+    return dispatch<double>(net, d, o, a0, tu.variant, tu.threads, tu.blocks_per_sm, next, st);
+  CellArgs a = a0;
+  a.retry = retry;
+  a.retry_count = rcount;
+  cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_error(e, "retry counter reset");
+  s = dispatch<float>(net, d, o, a, tu.variant, tu.threads, tu.blocks_per_sm, next, st);
+  if (s != MC_OK) return s;
+  // FP64 pass over the list; its length is read on the device
+  CellArgs b = a0;
+  b.index = retry;
+  b.n_dev = rcount;
+  b.n_cells = a0.n_cells;
+  return dispatch<double>(net, d, o, b, MC_VARIANT_PERSISTENT, tu.threads, tu.blocks_per_sm, next, st);
+}
+
+extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
+                                   double dt, double *x, int64_t ld, double *T, const double *ndens,
+                                   const double *rate_scale, int32_t *status, int32_t *stats,
+                                   void *stream) {
+  if (!net) return set_error(MC_E_INVALID, "mc_burn_batch: null network");
+  mc_burn_opts o;
+  mc_status s = check_opts(opts, &o);
+  if (s != MC_OK) return s;
+  if (n_cells < 0 || ld < n_cells || n_cells > (int64_t)INT32_MAX)
+    return set_error(MC_E_INVALID, "mc_burn_batch: need 0 <= n_cells <= ld and n_cells < 2^31");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(MC_E_INVALID, "mc_burn_batch: dt must be positive");
+  if (n_cells == 0) return MC_OK;
+  if (!x || !status) return set_error(MC_E_INVALID, "mc_burn_batch: x and status are required");
+  if (net->energy && !T) return set_error(MC_E_INVALID, "mc_burn_batch: energy networks need T");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != net->device) return set_error(MC_E_INVALID, "network lives on device %d, current is %d", net->device, dev);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool on_dev = is_device_ptr(x);
+  if (on_dev != is_device_ptr(status) || (T && on_dev != is_device_ptr(T)) ||
+      (ndens && on_dev != is_device_ptr(ndens)) || (rate_scale && on_dev != is_device_ptr(rate_scale)) ||
+      (stats && on_dev != is_device_ptr(stats)))
+    return set_error(MC_E_INVALID, "mc_burn_batch: mix of host and device arrays");
+  CellArgs a{};
+  a.n_cells = n_cells;
+  a.ld = ld;
+  a.dt = dt;
+  if (on_dev) {
+    a.x = x;
+    a.T = T;
+    a.nd = ndens;
+    a.ks = rate_scale;
+    a.status = status;
+    a.stats = stats;
+    return burn_device(net, o, a, st);
+  }
+  // host arrays: stage through device memory, packed with ld = n_cells
+  const int64_t nc = n_cells;
+  const size_t bx = sizeof(double) * net->S * nc, b1 = sizeof(double) * nc;
+  const size_t bks = rate_scale ? sizeof(double) * net->R * nc : 0;
+  const size_t bst = sizeof(int32_t) * nc, bsx = stats ? sizeof(int32_t) * MC_NSTAT * nc : 0;
+  char *buf = nullptr;
+  const size_t total = bx + (T ? b1 : 0) + (ndens ? b1 : 0) + bks + bst + bsx + 256 * 8;
+  cudaError_t e = cudaMallocAsync((void **)&buf, total, st);
+  if (e != cudaSuccess) return cuda_error(e, "staging allocation");
+  size_t off = 0;
+  auto take = [&](size_t b) { char *p = buf + off; off += (b + 255) & ~(size_t)255; return p; };
+  a.x = (double *)take(bx);
+  a.T = T ? (double *)take(b1) : nullptr;
+  a.nd = ndens ? (const double *)take(b1) : nullptr;
+  a.ks = rate_scale ? (const double *)take(bks) : nullptr;
+  a.status = (int32_t *)take(bst);
+  a.stats = stats ? (int32_t *)take(bsx) : nullptr;
+  a.ld = nc;
+  auto h2d = [&](void *dst, const void *src, int rows) -> cudaError_t {
+    return cudaMemcpy2DAsync(dst, sizeof(double) * nc, src, sizeof(double) * ld, sizeof(double) * nc, rows,
+                             cudaMemcpyHostToDevice, st);
+  };
+  e = h2d(a.x, x, net->S);
+  if (e == cudaSuccess && T) e = h2d(a.T, T, 1);
+  if (e == cudaSuccess && ndens) e = h2d((void *)a.nd, ndens, 1);
+  if (e == cudaSuccess && rate_scale) e = h2d((void *)a.ks, rate_scale, net->R);
+  if (e != cudaSuccess) { cudaFreeAsync(buf, st); return cuda_error(e, "host to device copy"); }
+  s = burn_device(net, o, a, st);
+  if (s != MC_OK) { cudaFreeAsync(buf, st); return s; }
+  e = cudaMemcpy2DAsync(x, sizeof(double) * ld, a.x, sizeof(double) * nc, sizeof(double) * nc, net->S,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && T)
+    e = cudaMemcpyAsync(T, a.T, b1, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status, a.status, bst, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && stats)
+    e = cudaMemcpy2DAsync(stats, sizeof(int32_t) * ld, a.stats, sizeof(int32_t) * nc, sizeof(int32_t) * nc,
+                          MC_NSTAT, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_error(e, "device to host copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "mc_burn_batch host round trip");
+  return MC_OK;
+}
