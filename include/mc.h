@@ -116,6 +116,9 @@ typedef struct {
     int32_t variant;        /* MC_VARIANT_* */
     int32_t block_threads;  /* threads per block, 0 = autotuned */
     int32_t blocks_per_sm;  /* persistent grid = blocks_per_sm x SMs, 0 = autotuned */
+    int32_t straggler_steps;/* persistent variant: a cell still running after this many
+                               attempts is finished by a whole warp (0 = default 2048,
+                               -1 = never) */
 } mc_burn_opts;
 
 void mc_burn_opts_default(mc_burn_opts *opts);
@@ -143,6 +146,24 @@ mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t
                         double dt, double *x, int64_t ld, double *T, const double *ndens,
                         const double *rate_scale, int32_t *status, int32_t *stats,
                         void *stream);
+
+/* Rate coefficients of every reaction at n temperatures T[c] (device
+ * arrays): kf[r * ld + c], kr[r * ld + c] (kr = 0 for irreversible reactions),
+ * computed by the burn's own device code (including its table-driven
+ * exponential). Asynchronous. Errors: MC_E_INVALID, MC_E_CUDA. */
+mc_status mc_network_rates(const mc_network *net, int64_t n, const double *T, double *kf, double *kr,
+                           int64_t ld, void *stream);
+
+/* Right-hand side f(y) (and, if jac != NULL, the analytic Jacobian) of the
+ * burn's ODE system at n states (device arrays): y[i * ld + c] with the
+ * energy form's last component u = (sum x) k_B T / (gamma - 1); T is the
+ * isothermal temperature (ignored by energy networks, NULL = 1), ndens and
+ * rate_scale as in mc_burn_batch; f[i * ld + c], jac[(i * n_ode + j) * ld + c];
+ * ok[c] = 0 where the state cannot be evaluated (T <= 0 or non-finite).
+ * Asynchronous. Errors: MC_E_INVALID, MC_E_CUDA. */
+mc_status mc_network_rhs(const mc_network *net, int64_t n, const double *y, int64_t ld, const double *T,
+                         const double *ndens, const double *rate_scale, double *f, double *jac, int32_t *ok,
+                         void *stream);
 
 /* One segment of a mixed batch: cells that share a network, laid out as in
  * mc_burn_batch (device pointers). */
@@ -174,6 +195,17 @@ mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, const mc_burn_
                           double dt, int64_t *totals, void *stream, mc_graph **out);
 mc_status mc_graph_launch(mc_graph *g, void *stream);
 mc_status mc_graph_destroy(mc_graph *g);
+
+/* Measure every launch shape (plain or persistent x threads per block x
+ * persistent blocks per SM) on a sample of n_sample cells (device arrays laid
+ * out as in mc_burn_batch; they are copied, not modified) and keep the fastest
+ * for this network size and opts->lu_precision: later burns whose shape
+ * fields are 0 use it. The winner is written to *best (may be NULL) and
+ * appended to the JSON-lines file named by the MC_AUTOTUNE_CACHE environment
+ * variable, which is read back on first use. Synchronous. */
+mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts, int64_t n_sample, double dt,
+                      const double *x, int64_t ld, const double *T, const double *ndens, void *stream,
+                      mc_burn_opts *best);
 
 /* ---------------------------------------------------------------- serving */
 /* A server keeps burn requests' state in a device pool, admits requests in
@@ -212,6 +244,11 @@ const char *mc_last_error(void);
 int32_t mc_version(void);
 /* Kernel launches issued by this thread since the last reset (for accounting). */
 int64_t mc_launch_count(int32_t reset);
+/* Measure the fused multiply-add rate (TFLOP/s, 2 flops per FMA) of the
+ * current device in FP64 and FP32 with dependent-free FMA chains over every SM
+ * (about 10 ms each): the ceiling this ALU-bound burn is reported against.
+ * Either pointer may be NULL. Synchronous. Errors: MC_E_CUDA, MC_E_NOMEM. */
+mc_status mc_probe_fma_rate(double *tflops_fp64, double *tflops_fp32);
 
 #ifdef __cplusplus
 }

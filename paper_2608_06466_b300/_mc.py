@@ -42,7 +42,7 @@ class mc_network_desc(C.Structure):
 class mc_burn_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_order", C.c_int32),
                 ("max_steps", C.c_int32), ("lu_precision", C.c_int32), ("variant", C.c_int32),
-                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32)]
+                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("straggler_steps", C.c_int32)]
 
 
 class mc_segment(C.Structure):
@@ -87,6 +87,13 @@ _sig("mc_server_destroy", C.c_int32, [C.c_void_p])
 _sig("mc_last_error", C.c_char_p, [])
 _sig("mc_version", C.c_int32, [])
 _sig("mc_launch_count", C.c_int64, [C.c_int32])
+_sig("mc_network_rates", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                     C.c_void_p])
+_sig("mc_network_rhs", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p])
+_sig("mc_autotune", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p, C.c_int64,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(mc_burn_opts)])
+_sig("mc_probe_fma_rate", C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_double)])
 
 
 class MCError(RuntimeError):
@@ -258,6 +265,31 @@ class Server:
 
 def mc_server_create(device=0, hbm_budget_bytes=150 << 30, opts=None) -> Server:
     return Server(device, hbm_budget_bytes, opts)
+
+
+def mc_network_rates(net: Network, n, T, kf, kr, ld, stream=None) -> int:
+    return check(lib.mc_network_rates(net.handle, int(n), _ptr(T), _ptr(kf), _ptr(kr), int(ld), _stream_ptr(stream)),
+                 "mc_network_rates")
+
+
+def mc_network_rhs(net: Network, n, y, ld, T, ndens, rate_scale, f, jac, ok, stream=None) -> int:
+    return check(lib.mc_network_rhs(net.handle, int(n), _ptr(y), int(ld), _ptr(T), _ptr(ndens), _ptr(rate_scale),
+                                    _ptr(f), _ptr(jac), _ptr(ok), _stream_ptr(stream)), "mc_network_rhs")
+
+
+def mc_autotune(net: Network, opts, n_sample, dt, x, ld, T, ndens, stream=None) -> mc_burn_opts:
+    o = opts if opts is not None else mc_burn_opts_default()
+    best = mc_burn_opts()
+    check(lib.mc_autotune(net.handle, C.byref(o), int(n_sample), float(dt), _ptr(x), int(ld), _ptr(T), _ptr(ndens),
+                          _stream_ptr(stream), C.byref(best)), "mc_autotune")
+    return best
+
+
+def mc_probe_fma_rate():
+    """(FP64, FP32) fused multiply-add rate of the current device in TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    check(lib.mc_probe_fma_rate(C.byref(a), C.byref(b)), "mc_probe_fma_rate")
+    return a.value, b.value
 
 
 def mc_launch_count(reset: bool = False) -> int:

@@ -1,16 +1,173 @@
-// mc_autotune.cu -- launch-shape selection (variant, threads per block,
-// persistent blocks per SM) per network size and matrix precision.
+// mc_autotune.cu -- measured launch-shape selection. mc_autotune times every
+// candidate (variant x threads per block x persistent blocks per SM) on a
+// sample of the caller's cells and keeps the fastest per (device, ODE count,
+// reactions, energy form, matrix precision); mc_burn_* with zero shape fields
+// use the stored winner. Winners persist in a JSON-lines file when
+// MC_AUTOTUNE_CACHE names one.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
 
 #include "mc_internal.h"
+#include "mc_kernels.cuh"
 
 using namespace mc;
 
+namespace {
+using Key = std::tuple<std::string, int, int, int, int>;
+std::mutex g_mu;
+std::map<Key, Tuned> g_table;
+bool g_loaded = false;
+
+std::string device_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+  std::string s = p.name;
+  for (char &c : s)
+    if (c == ' ' || c == '"') c = '_';
+  return s;
+}
+
+Key key_of(const mc_network *net, int lu) {
+  return Key(device_name(), net ? net->n : 0, net ? net->R : 0, net ? net->energy : 0, lu);
+}
+
+void load_cache() {
+  if (g_loaded) return;
+  g_loaded = true;
+  const char *path = std::getenv("MC_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    char dev[256];
+    int n, R, en, lu, var, thr, bps;
+    if (std::sscanf(line,
+                    "{\"device\": \"%255[^\"]\", \"n\": %d, \"R\": %d, \"energy\": %d, \"lu\": %d, "
+                    "\"variant\": %d, \"threads\": %d, \"blocks_per_sm\": %d}",
+                    dev, &n, &R, &en, &lu, &var, &thr, &bps) == 8)
+      g_table[Key(dev, n, R, en, lu)] = Tuned{var, thr, bps, 2048};
+  }
+  std::fclose(f);
+}
+
+void save_entry(const Key &k, const Tuned &t) {
+  const char *path = std::getenv("MC_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f,
+               "{\"device\": \"%s\", \"n\": %d, \"R\": %d, \"energy\": %d, \"lu\": %d, \"variant\": %d, "
+               "\"threads\": %d, \"blocks_per_sm\": %d}\n",
+               std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), t.variant,
+               t.threads, t.blocks_per_sm);
+  std::fclose(f);
+}
+}  // namespace
+
 Tuned mc::autotune_pick(const mc_network *net, const mc_burn_opts &o) {
-  (void)net;
-  Tuned t;
-  t.variant = o.variant == MC_VARIANT_AUTO ? MC_VARIANT_PERSISTENT : o.variant;
-  t.threads = o.block_threads ? o.block_threads : 128;
-  t.blocks_per_sm = o.blocks_per_sm ? o.blocks_per_sm : 2;
+  Tuned t{MC_VARIANT_PERSISTENT, 128, 2, 2048};
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_cache();
+    auto it = g_table.find(key_of(net, o.lu_precision));
+    if (it != g_table.end()) t = it->second;
+  }
+  if (o.variant != MC_VARIANT_AUTO) t.variant = o.variant;
+  if (o.block_threads) t.threads = o.block_threads;
+  if (o.blocks_per_sm) t.blocks_per_sm = o.blocks_per_sm;
+  if (o.straggler_steps) t.strag_steps = o.straggler_steps;
   return t;
+}
+
+extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts, int64_t n_sample, double dt,
+                                 const double *x, int64_t ld, const double *T, const double *ndens,
+                                 void *stream, mc_burn_opts *best) {
+  if (!net || !x || n_sample <= 0 || ld < n_sample || (net->energy && !T))
+    return set_error(MC_E_INVALID, "mc_autotune: bad arguments");
+  mc_burn_opts o;
+  mc_status s = check_opts(opts, &o);
+  if (s != MC_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = n_sample;
+  double *wx = nullptr, *wT = nullptr;
+  int32_t *ws = nullptr;
+  cudaError_t e = cudaMalloc(&wx, sizeof(double) * net->S * n);
+  if (e == cudaSuccess && T) e = cudaMalloc(&wT, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&ws, sizeof(int32_t) * n);
+  if (e != cudaSuccess) {
+    cudaFree(wx);
+    cudaFree(wT);
+    return cuda_error(e, "autotune buffers");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  struct Cand { int var, thr, bps; };
+  std::vector<Cand> cands;
+  for (int thr : {64, 128, 256}) cands.push_back({MC_VARIANT_PLAIN, thr, 0});
+  for (int thr : {64, 128, 256})
+    for (int bps : {1, 2, 4}) cands.push_back({MC_VARIANT_PERSISTENT, thr, bps});
+  float best_ms = 1e30f;
+  Cand win = cands[0];
+  for (const Cand &c : cands) {
+    e = cudaMemcpy2DAsync(wx, sizeof(double) * n, x, sizeof(double) * ld, sizeof(double) * n, net->S,
+                          cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && T) e = cudaMemcpyAsync(wT, T, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) break;
+    mc_burn_opts t = o;
+    t.variant = c.var;
+    t.block_threads = c.thr;
+    t.blocks_per_sm = c.bps ? c.bps : 1;
+    CellArgs a{};
+    a.n_cells = n;
+    a.ld = n;
+    a.dt = dt;
+    a.x = wx;
+    a.T = wT;
+    a.nd = ndens;
+    a.status = ws;
+    cudaEventRecord(e0, st);
+    s = burn_device(net, t, a, st);
+    cudaEventRecord(e1, st);
+    if (s != MC_OK) break;
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      win = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(wx);
+  cudaFree(wT);
+  cudaFree(ws);
+  if (s != MC_OK) return s;
+  if (e != cudaSuccess) return cuda_error(e, "autotune trial");
+  Tuned t{win.var, win.thr, win.bps ? win.bps : 1, 2048};
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_cache();
+    const Key k = key_of(net, o.lu_precision);
+    g_table[k] = t;
+    save_entry(k, t);
+  }
+  if (best) {
+    *best = o;
+    best->variant = t.variant;
+    best->block_threads = t.threads;
+    best->blocks_per_sm = t.blocks_per_sm;
+  }
+  return MC_OK;
 }

@@ -66,7 +66,50 @@ struct DNet {
   double gm1;            // gamma - 1
   const int4 *side;      // (reactant0, reactant1, product0, product1), -1 = empty
   const RxPar *par;
+  const double *exptab;  // 2^(j/64), j = 0..63 (for rexp)
+  // per-species occurrence lists: species i appears in slots csr_ent[csr_ptr[i]
+  // .. csr_ptr[i+1]) with entry = 4 r + slot (slots 0,1 reactants, 2,3 products),
+  // in the order the thread right-hand side applies them
+  const int *csr_ptr;
+  const int *csr_ent;
 };
+
+// Table-driven exponential for the rate coefficients (the dominant FP64 cost
+// of the burn): x = (n/64) ln 2 + r with n = round(64 x / ln 2) (obtained by
+// adding 1.5 * 2^52, which leaves n in the low mantissa bits), r reduced with
+// a two-part ln2/64 in two FMAs, |r| <= ln2/128; exp(r) - 1 by its Taylor
+// polynomial to degree 5 (truncation below 4e-17 relative on that interval);
+// exp(x) = 2^(n >> 6) * (T + T (exp(r) - 1)), T = 2^((n & 63)/64) from a
+// 64-entry table computed on the host, the power of two applied to the
+// exponent field. About 11 FP64 instructions; within a few ulp of the
+// correctly rounded value (checked against the CUDA exp in the tests).
+__device__ __forceinline__ double rexp(double x, const double *tab) {
+  if (!(x > -745.2)) return (x != x) ? x : 0.0;      // NaN propagates; -inf and underflow give 0
+  if (x > 709.78) return __longlong_as_double(0x7ff0000000000000ll);
+  const double SHIFT = 6755399441055744.0;           // 1.5 * 2^52
+  const double INVL = 92.332482616893656768;        // 64 / ln 2
+  const double L_HI = 0.010830424696249145;         // ln 2 / 64, leading part
+  const double L_LO = 3.623510646634843e-19;         // ln 2 / 64 - L_HI
+  const double kd = fma(x, INVL, SHIFT);
+  const int n = __double2loint(kd);
+  const double nd = kd - SHIFT;
+  double r = fma(-nd, L_HI, x);
+  r = fma(-nd, L_LO, r);
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = p * r;
+  const double t = __ldg(&tab[n & 63]);
+  double v = fma(t, p, t);
+  const int m = n >> 6;
+  if (m >= -1021) {
+    return __hiloint2double(__double2hiint(v) + (m << 20), __double2loint(v));
+  }
+  // result below the normal range: scale in two steps so the rounding happens once
+  v = __hiloint2double(__double2hiint(v) + ((m + 600) << 20), __double2loint(v));
+  return v * 2.409919865102884e-181;                 // 2^-600
+}
 
 // per-cell inputs the right-hand side needs
 struct CellIn {
@@ -98,9 +141,9 @@ __device__ __forceinline__ bool net_rhs(const DNet &net, const CellIn &c, const 
     const int4 s = __ldg(&net.side[r]);
     const RxPar &p = net.par[r];
     const double lnAf = __ldg(&p.lnAf), bf = __ldg(&p.bf), Cf = __ldg(&p.Cf);
-    double kf = exp(lnAf + bf * lnT - Cf * invT);
+    double kf = rexp(lnAf + bf * lnT - Cf * invT, net.exptab);
     double kr = 0.0;
-    if (__ldg(&p.rev) != 0.0) kr = exp(__ldg(&p.lnAr) + __ldg(&p.br) * lnT - __ldg(&p.Cr) * invT);
+    if (__ldg(&p.rev) != 0.0) kr = rexp(__ldg(&p.lnAr) + __ldg(&p.br) * lnT - __ldg(&p.Cr) * invT, net.exptab);
     if (c.ks) {
       const double sc = c.ks[r * c.ks_ld];
       kf *= sc;
@@ -147,12 +190,12 @@ __device__ __forceinline__ bool net_jac(const DNet &net, const CellIn &c, const 
     const int4 s = __ldg(&net.side[r]);
     const RxPar &p = net.par[r];
     const double bf = __ldg(&p.bf), Cf = __ldg(&p.Cf);
-    double kf = exp(__ldg(&p.lnAf) + bf * lnT - Cf * invT);
+    double kf = rexp(__ldg(&p.lnAf) + bf * lnT - Cf * invT, net.exptab);
     double kr = 0.0, br = 0.0, Cr = 0.0;
     if (__ldg(&p.rev) != 0.0) {
       br = __ldg(&p.br);
       Cr = __ldg(&p.Cr);
-      kr = exp(__ldg(&p.lnAr) + br * lnT - Cr * invT);
+      kr = rexp(__ldg(&p.lnAr) + br * lnT - Cr * invT, net.exptab);
     }
     if (c.ks) {
       const double sc = c.ks[r * c.ks_ld];
@@ -279,10 +322,14 @@ struct Lane {
   double l[QMAX + 1];
   double hist[QMAX + 3];   // accepted step sizes, most recent first
   double t, h, tend, crate, gamma_p, gamma, cq, esave_h, delp, eta_max, h0;
+  double eta_pend;         // Nordsieck rescale factor the next begin_step applies
+  double dsm;              // local-error norm of the last converged attempt
   CellIn cin;
   int64_t cell;
   int q, qwait, nef, ncf, jage, page, attempts, m, phase, status;
+  int todo;                // next stage (Todo)
   bool need_j, need_p, jcur, have_es, last;
+  bool kept;               // hand-off refused (record list full): finish here
   int st[NSTAT];
 };
 
@@ -329,23 +376,32 @@ __device__ __forceinline__ void retract(Lane<N, LT> &L, int n) {
         if (i < n) L.z[j - 1][i] -= L.z[j][i];
 }
 
-// xi_j = (sum of the first j gaps)/h for j = 1..m
+// xi_j = (sum of the first j gaps)/h for j = 1..m (m <= QMAX + 2); loops are
+// unrolled over the fixed maximum so the small arrays stay in registers
 __device__ __forceinline__ void xi_of(double h, const double *gaps, int m, double *xi) {
   double s = 0.0;
-  for (int j = 0; j < m; ++j) {
-    s += gaps[j];
-    xi[j] = s / h;
-  }
+#pragma unroll
+  for (int j = 0; j < QMAX + 2; ++j)
+    if (j < m) {
+      s += gaps[j];
+      xi[j] = s / h;
+    }
 }
 
-// coefficients of x * prod_{i<k}(x + xi_i), k = number of factors (c[0..k])
+// coefficients of x * prod_{i<k}(x + xi_i), k = number of factors (c[0..k], k <= QMAX + 1)
 __device__ __forceinline__ void shifted_product(int k, const double *xi, double *c) {
-  for (int j = 0; j <= k; ++j) c[j] = 0.0;
+#pragma unroll
+  for (int j = 0; j < QMAX + 2; ++j) c[j] = 0.0;
   c[1] = 1.0;
-  for (int i = 1; i <= k - 1; ++i) {
-    const double a = xi[i - 1];
-    for (int j = i + 1; j >= 1; --j) c[j] = c[j - 1] + a * c[j];
-    c[0] = a * c[0];
+#pragma unroll
+  for (int i = 1; i <= QMAX; ++i) {
+    if (i <= k - 1) {
+      const double a = xi[i - 1];
+#pragma unroll
+      for (int j = QMAX + 1; j >= 1; --j)
+        if (j <= i + 1) c[j] = c[j - 1] + a * c[j];
+      c[0] = a * c[0];
+    }
   }
 }
 
@@ -355,17 +411,34 @@ __device__ __forceinline__ double harmonic(int k) {
   return s;
 }
 
+// ---- step logic, staged ---------------------------------------------------
+// advance() consumes f(y) and only records what the lane needs next (L.todo);
+// run_stages() then runs each stage of the step logic from ONE call site, so
+// lanes that reached the same stage by different paths execute it together
+// once per loop trip instead of once per path. Factors that rescale the
+// Nordsieck array are applied by begin_step (after the stage's own order
+// change), in the same order the method defines: the stage's factor, then the
+// final-step clip.
+enum Todo : int { TD_NONE = 0, TD_BEGIN, TD_CONVERGED, TD_CONVFAIL, TD_REJECT, TD_ACCEPT, TD_SELECT };
+
 template <int N, typename LT>
 __device__ __forceinline__ void finish(Lane<N, LT> &L, int status) {
   L.status = status;
   L.phase = PH_DONE;
+  L.todo = TD_NONE;
 }
 
-// Start a step attempt (or finish the cell): clip the last step to t_end,
-// weights from the accepted state, predict, variable-step coefficients.
+// Start a step attempt (or finish the cell): pending rescale, clip the last
+// step to t_end, weights from the accepted state, predict, variable-step
+// coefficients.
 template <int N, typename LT>
-__device__ void begin_step(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+__device__ __forceinline__ void begin_step(Lane<N, LT> &L, const DNet &net, const Opts &o) {
   const int n = net.n;
+  L.todo = TD_NONE;
+  if (L.eta_pend != 1.0) {
+    rescale(L, n, L.eta_pend);
+    L.eta_pend = 1.0;
+  }
   if (!(L.t < L.tend)) { finish(L, CELL_OK); return; }
   if (L.attempts >= o.max_steps) { finish(L, CELL_MAX_STEPS); return; }
   L.last = false;
@@ -383,17 +456,30 @@ __device__ void begin_step(Lane<N, LT> &L, const DNet &net, const Opts &o) {
   const int q = L.q;
   double gaps[QMAX + 2], xi[QMAX + 2];
   gaps[0] = L.h;
-  for (int k = 0; k < q; ++k) gaps[k + 1] = L.hist[k];
+#pragma unroll
+  for (int k = 0; k < QMAX + 1; ++k) gaps[k + 1] = L.hist[k];
   xi_of(L.h, gaps, q + 1, xi);
   // l = coefficients of prod_{j<=q} (1 + x/xi_j)
-  for (int k = 0; k <= q; ++k) L.l[k] = 0.0;
-  L.l[0] = 1.0;
-  for (int j = 1; j <= q; ++j) {
-    const double c = 1.0 / xi[j - 1];
-    for (int k = j; k >= 1; --k) L.l[k] += c * L.l[k - 1];
-  }
-  L.cq = (1.0 / xi[q]) / L.l[1];
-  L.gamma = L.h / L.l[1];
+  double l[QMAX + 1];
+#pragma unroll
+  for (int k = 0; k <= QMAX; ++k) l[k] = 0.0;
+  l[0] = 1.0;
+#pragma unroll
+  for (int j = 1; j <= QMAX; ++j)
+    if (j <= q) {
+      const double c = 1.0 / xi[j - 1];
+#pragma unroll
+      for (int k = QMAX; k >= 1; --k)
+        if (k <= j) l[k] += c * l[k - 1];
+    }
+  double xq = xi[0];
+#pragma unroll
+  for (int j = 1; j <= QMAX; ++j)
+    if (j == q) xq = xi[j];
+#pragma unroll
+  for (int k = 0; k <= QMAX; ++k) L.l[k] = l[k];
+  L.cq = (1.0 / xq) / l[1];
+  L.gamma = L.h / l[1];
   L.jcur = false;
   L.m = 0;
 #pragma unroll
@@ -405,23 +491,7 @@ __device__ void begin_step(Lane<N, LT> &L, const DNet &net, const Opts &o) {
   L.phase = PH_NEWTON;
 }
 
-template <int N, typename LT>
-__device__ void conv_failure(Lane<N, LT> &L, const DNet &net, const Opts &o) {
-  const int n = net.n;
-  retract(L, n);
-  L.ncf += 1;
-  L.st[ST_CONV_FAILS] += 1;
-  if (L.ncf >= MXNCF) { finish(L, CELL_CONV_FAIL); return; }
-  rescale(L, n, ETACF);
-  L.h *= ETACF;
-  L.need_p = true;
-  L.qwait = L.q + 1;
-  L.have_es = false;
-  if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
-  begin_step(L, net, o);
-}
-
-// Order change helper: drop q -> q-1 (z_j -= c_j z_q) with xi at the array's point.
+// Order drop q -> q-1 (z_j -= c_j z_q) with xi at the array's point.
 template <int N, typename LT>
 __device__ __forceinline__ void lower_order(Lane<N, LT> &L, int n, const double *xi) {
   double c[QMAX + 2];
@@ -434,54 +504,86 @@ __device__ __forceinline__ void lower_order(Lane<N, LT> &L, int n, const double 
   L.q = q - 1;
 }
 
+// est_{q-1} coefficient prod_{j<q} xi_j / sum_{j<q} 1/xi_j
+__device__ __forceinline__ double qm1_coef(int q, const double *xi) {
+  double prod = 1.0, l1 = 0.0;
+#pragma unroll
+  for (int j = 1; j <= QMAX; ++j)
+    if (j <= q - 1) {
+      prod *= xi[j - 1];
+      l1 += 1.0 / xi[j - 1];
+    }
+  return prod / l1;
+}
+
+// Newton failure: undo the prediction, cut h by ETACF.
 template <int N, typename LT>
-__device__ void after_convergence(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+__device__ __forceinline__ void stage_conv_failure(Lane<N, LT> &L, const DNet &net) {
+  retract(L, net.n);
+  L.ncf += 1;
+  L.st[ST_CONV_FAILS] += 1;
+  if (L.ncf >= MXNCF) { finish(L, CELL_CONV_FAIL); return; }
+  L.eta_pend = ETACF;
+  L.h *= ETACF;
+  L.need_p = true;
+  L.qwait = L.q + 1;
+  L.have_es = false;
+  if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
+  L.todo = TD_BEGIN;
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void stage_error_test(Lane<N, LT> &L, const DNet &net) {
+  L.dsm = L.cq * wrms<N>(net.n, L.e, L.iw);
+  L.todo = (L.dsm > 1.0) ? TD_REJECT : TD_ACCEPT;
+}
+
+// Local-error test failed: undo the prediction, then a smaller step (maybe
+// one order lower), or after KFC failures a restart at order 1 (needs f(z_0)).
+template <int N, typename LT>
+__device__ __forceinline__ void stage_reject(Lane<N, LT> &L, const DNet &net) {
   const int n = net.n;
   const int q = L.q;
-  const double dsm = L.cq * wrms<N>(n, L.e, L.iw);
-  double xi[QMAX + 2];
-  if (dsm > 1.0) {
-    // ---- error test failed
-    retract(L, n);
-    L.nef += 1;
-    L.st[ST_ERR_FAILS] += 1;
-    L.have_es = false;
-    if (L.nef >= KFC) {
-      // restart at order 1 from the accepted state: needs f(z_0)
+  retract(L, n);
+  L.nef += 1;
+  L.st[ST_ERR_FAILS] += 1;
+  L.have_es = false;
+  if (L.nef >= KFC) {
 #pragma unroll
-      for (int i = 0; i < N; ++i)
-        if (i < n) L.y[i] = L.z[0][i];
-      L.phase = PH_RESTART;
-      return;
-    }
-    double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
-    int qn = q;
-    if (q > 1) {
-      xi_of(L.h, L.hist, q, xi);
-      double prod = 1.0, l1 = 0.0;
-      for (int j = 1; j <= q - 1; ++j) {
-        prod *= xi[j - 1];
-        l1 += 1.0 / xi[j - 1];
-      }
-      const double est = (prod / l1) * wrms<N>(n, L.z[q], L.iw);
-      const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
-      if (eta_m > eta) { eta = eta_m; qn = q - 1; }
-    }
-    eta = fmax(ETAMIN, fmin(eta, 1.0));
-    if (qn < q) lower_order(L, n, xi);
-    rescale(L, n, eta);
-    L.h *= eta;
-    L.qwait = L.q + 1;
-    if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
-    begin_step(L, net, o);
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.y[i] = L.z[0][i];
+    L.phase = PH_RESTART;
+    L.todo = TD_NONE;
     return;
   }
-  // ---- accept
+  double eta = 1.0 / (pow(BIAS_Q * L.dsm, 1.0 / (q + 1)) + ADDON);
+  int qn = q;
+  double xi[QMAX + 2];
+  if (q > 1) {
+    xi_of(L.h, L.hist, q, xi);
+    const double est = qm1_coef(q, xi) * wrms<N>(n, L.z[q], L.iw);
+    const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
+    if (eta_m > eta) { eta = eta_m; qn = q - 1; }
+  }
+  eta = fmax(ETAMIN, fmin(eta, 1.0));
+  if (qn < q) lower_order(L, n, xi);
+  L.eta_pend = eta;
+  L.h *= eta;
+  L.qwait = L.q + 1;
+  if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
+  L.todo = TD_BEGIN;
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void stage_accept(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+  const int n = net.n;
+  const int q = L.q;
   for (int j = 0; j <= q; ++j)
 #pragma unroll
     for (int i = 0; i < N; ++i)
       if (i < n) L.z[j][i] += L.l[j] * L.e[i];
   L.t = L.last ? L.tend : L.t + L.h;
+#pragma unroll
   for (int k = QMAX + 2; k > 0; --k) L.hist[k] = L.hist[k - 1];
   L.hist[0] = L.h;
   L.st[ST_STEPS] += 1;
@@ -498,18 +600,20 @@ __device__ void after_convergence(Lane<N, LT> &L, const DNet &net, const Opts &o
     L.have_es = true;
   }
   if (L.last) { finish(L, CELL_OK); return; }
-  if (L.qwait > 0) { begin_step(L, net, o); return; }
-  // ---- step size and order selection
-  double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
+  L.todo = (L.qwait > 0) ? TD_BEGIN : TD_SELECT;
+}
+
+// Step size and order selection from the q-1, q, q+1 estimates.
+template <int N, typename LT>
+__device__ __forceinline__ void stage_select(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+  const int n = net.n;
+  const int q = L.q;
+  double xi[QMAX + 2];
+  double eta = 1.0 / (pow(BIAS_Q * L.dsm, 1.0 / (q + 1)) + ADDON);
   int qn = q;
   xi_of(L.h, L.hist, q + 1, xi);
   if (q > 1) {
-    double prod = 1.0, l1 = 0.0;
-    for (int j = 1; j <= q - 1; ++j) {
-      prod *= xi[j - 1];
-      l1 += 1.0 / xi[j - 1];
-    }
-    const double est = (prod / l1) * wrms<N>(n, L.z[q], L.iw);
+    const double est = qm1_coef(q, xi) * wrms<N>(n, L.z[q], L.iw);
     const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
     if (eta_m > eta) { eta = eta_m; qn = q - 1; }
   }
@@ -523,16 +627,18 @@ __device__ void after_convergence(Lane<N, LT> &L, const DNet &net, const Opts &o
     if (eta_p > eta) { eta = eta_p; qn = q + 1; }
   }
   L.have_es = false;
+  L.todo = TD_BEGIN;
   if (eta < THRESH) {
     L.qwait = 2;
-    begin_step(L, net, o);
     return;
   }
   eta = fmin(eta, L.eta_max);
   L.eta_max = ETAMX;
   if (qn > q) {
     double prod = 1.0, c[QMAX + 2];
-    for (int j = 1; j <= q + 1; ++j) prod *= xi[j - 1];
+#pragma unroll
+    for (int j = 1; j <= QMAX + 1; ++j)
+      if (j <= q + 1) prod *= xi[j - 1];
     const double C = 1.0 / prod;
     shifted_product(q + 1, xi, c);
 #pragma unroll
@@ -546,16 +652,15 @@ __device__ void after_convergence(Lane<N, LT> &L, const DNet &net, const Opts &o
   } else if (qn < q) {
     lower_order(L, n, xi);
   }
-  rescale(L, n, eta);
+  L.eta_pend = eta;
   L.h *= eta;
   L.qwait = L.q + 1;
-  begin_step(L, net, o);
 }
 
 // One modified-Newton correction with f = f(y) just evaluated.
 // 0 = continue, 1 = converged, 2 = failed, 3 = failed (could not evaluate)
 template <int N, typename LT>
-__device__ int newton_iter(Lane<N, LT> &L, const DNet &net, bool ok) {
+__device__ __forceinline__ int newton_iter(Lane<N, LT> &L, const DNet &net, bool ok) {
   const int n = net.n;
   if (!ok) return 3;
   L.st[ST_RHS] += 1;
@@ -612,99 +717,108 @@ __device__ int newton_iter(Lane<N, LT> &L, const DNet &net, bool ok) {
   return 0;
 }
 
-// Consume f(y) according to the lane's phase and prepare the next y.
+// Consume f(y) according to the lane's phase; record what comes next.
 template <int N, typename LT>
-__device__ void advance(Lane<N, LT> &L, const DNet &net, const Opts &o, bool ok) {
+__device__ __forceinline__ void advance(Lane<N, LT> &L, const DNet &net, const Opts &o, bool ok) {
   const int n = net.n;
-  switch (L.phase) {
-    case PH_F0: {
-      if (!ok) { finish(L, CELL_BAD_INPUT); return; }
-      L.st[ST_RHS] += 1;
-      // starting step (Hairer, Norsett & Wanner, Solving ODEs I, II.4), p = 1
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-        if (i < n) L.iw[i] = 1.0 / (o.rtol * fabs(L.z[0][i]) + o.atol);
-      const double d0 = wrms<N>(n, L.z[0], L.iw), d1 = wrms<N>(n, L.f, L.iw);
-      double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
-      h0 = fmin(h0, L.tend);
-      L.h0 = h0;
+  L.todo = TD_NONE;
+  if (L.phase == PH_NEWTON) {
+    const int r = newton_iter<N, LT>(L, net, ok);
+    if (r == 0) return;
+    if (r == 1) { L.todo = TD_CONVERGED; return; }
+    if (r == 2 && !L.jcur) {
+      // stale Jacobian: refresh it and redo the corrector from the prediction
+      L.need_j = true;
+      L.m = 0;
 #pragma unroll
       for (int i = 0; i < N; ++i)
         if (i < n) {
-          L.e[i] = L.f[i];  // f0 parked in e
-          L.y[i] = L.z[0][i] + h0 * L.f[i];
+          L.e[i] = 0.0;
+          L.y[i] = L.z[0][i];
         }
-      L.st[ST_RHS] += 1;
-      L.phase = PH_HW;
       return;
     }
-    case PH_HW: {
-      double h = L.h0;
-      if (ok) {
-        double dv[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) dv[i] = (i < n) ? L.f[i] - L.e[i] : 0.0;
-        const double d1 = wrms<N>(n, L.e, L.iw);
-        const double d2 = wrms<N>(n, dv, L.iw) / L.h0;
-        const double dm = fmax(d1, d2);
-        const double h1 = (dm <= 1e-15) ? fmax(1e-6, L.h0 * 1e-3) : sqrt(0.01 / dm);
-        h = fmin(fmin(100.0 * L.h0, h1), L.tend);
-      }
-      L.h = h;
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-        if (i < n) L.z[1][i] = h * L.e[i];
-      L.t = 0.0;
-      L.q = 1;
-      L.qwait = 2;
-      for (int k = 0; k < QMAX + 3; ++k) L.hist[k] = h;
-      L.need_j = true;
-      L.need_p = true;
-      L.crate = CRATE0;
-      L.gamma_p = 1.0;
-      L.eta_max = ETAMX_FIRST;
-      L.nef = L.ncf = 0;
-      L.jage = L.page = 0;
-      L.have_es = false;
-      L.attempts = 0;
-      begin_step(L, net, o);
-      return;
-    }
-    case PH_NEWTON: {
-      const int r = newton_iter<N, LT>(L, net, ok);
-      if (r == 0) return;
-      if (r == 1) { after_convergence(L, net, o); return; }
-      if (r == 2 && !L.jcur) {
-        // stale Jacobian: refresh it and redo the corrector from the prediction
-        L.need_j = true;
-        L.m = 0;
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-          if (i < n) {
-            L.e[i] = 0.0;
-            L.y[i] = L.z[0][i];
-          }
-        return;
-      }
-      conv_failure(L, net, o);
-      return;
-    }
-    case PH_RESTART: {
-      if (!ok) { finish(L, CELL_NONFINITE); return; }
-      L.st[ST_RHS] += 1;
-      L.h *= ETAMIN;
-      L.q = 1;
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-        if (i < n) L.z[1][i] = L.h * L.f[i];
-      L.qwait = 2;
-      if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
-      begin_step(L, net, o);
-      return;
-    }
-    default:
-      return;
+    L.todo = TD_CONVFAIL;
+    return;
   }
+  if (L.phase == PH_F0) {
+    if (!ok) { finish(L, CELL_BAD_INPUT); return; }
+    L.st[ST_RHS] += 1;
+    // starting step (Hairer, Norsett & Wanner, Solving ODEs I, II.4), p = 1
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.iw[i] = 1.0 / (o.rtol * fabs(L.z[0][i]) + o.atol);
+    const double d0 = wrms<N>(n, L.z[0], L.iw), d1 = wrms<N>(n, L.f, L.iw);
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+    h0 = fmin(h0, L.tend);
+    L.h0 = h0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) {
+        L.e[i] = L.f[i];  // f0 parked in e
+        L.y[i] = L.z[0][i] + h0 * L.f[i];
+      }
+    L.st[ST_RHS] += 1;
+    L.phase = PH_HW;
+    return;
+  }
+  if (L.phase == PH_HW) {
+    double h = L.h0;
+    if (ok) {
+      double dv[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) dv[i] = (i < n) ? L.f[i] - L.e[i] : 0.0;
+      const double d1 = wrms<N>(n, L.e, L.iw);
+      const double d2 = wrms<N>(n, dv, L.iw) / L.h0;
+      const double dm = fmax(d1, d2);
+      const double h1 = (dm <= 1e-15) ? fmax(1e-6, L.h0 * 1e-3) : sqrt(0.01 / dm);
+      h = fmin(fmin(100.0 * L.h0, h1), L.tend);
+    }
+    L.h = h;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.z[1][i] = h * L.e[i];
+    L.t = 0.0;
+    L.q = 1;
+    L.qwait = 2;
+#pragma unroll
+    for (int k = 0; k < QMAX + 3; ++k) L.hist[k] = h;
+    L.need_j = true;
+    L.need_p = true;
+    L.crate = CRATE0;
+    L.gamma_p = 1.0;
+    L.eta_max = ETAMX_FIRST;
+    L.eta_pend = 1.0;
+    L.nef = L.ncf = 0;
+    L.jage = L.page = 0;
+    L.have_es = false;
+    L.attempts = 0;
+    L.todo = TD_BEGIN;
+    return;
+  }
+  if (L.phase == PH_RESTART) {
+    if (!ok) { finish(L, CELL_NONFINITE); return; }
+    L.st[ST_RHS] += 1;
+    L.h *= ETAMIN;
+    L.q = 1;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) L.z[1][i] = L.h * L.f[i];
+    L.qwait = 2;
+    if (L.t + L.h == L.t) { finish(L, CELL_H_UNDERFLOW); return; }
+    L.todo = TD_BEGIN;
+  }
+}
+
+// The stages, each from exactly one call site.
+template <int N, typename LT>
+__device__ __forceinline__ void run_stages(Lane<N, LT> &L, const DNet &net, const Opts &o) {
+  if (L.todo == TD_CONVFAIL) stage_conv_failure(L, net);
+  if (L.todo == TD_CONVERGED) stage_error_test(L, net);
+  if (L.todo == TD_REJECT) stage_reject(L, net);
+  if (L.todo == TD_ACCEPT) stage_accept(L, net, o);
+  if (L.todo == TD_SELECT) stage_select(L, net, o);
+  if (L.todo == TD_BEGIN) begin_step(L, net, o);
 }
 
 }  // namespace mc

@@ -2,8 +2,8 @@
 #include "mc_launch.cuh"
 
 namespace mc {
-template mc_status launch_one<33, double>(const DNet &, const Opts &, const CellArgs &, int, int, int,
+template mc_status launch_one<33, double>(const DNet &, const Opts &, const CellArgs &, int, int, int, int,
                                           unsigned long long *, cudaStream_t);
-template mc_status launch_one<33, float>(const DNet &, const Opts &, const CellArgs &, int, int, int,
+template mc_status launch_one<33, float>(const DNet &, const Opts &, const CellArgs &, int, int, int, int,
                                          unsigned long long *, cudaStream_t);
 }  // namespace mc

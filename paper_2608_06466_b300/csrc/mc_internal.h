@@ -21,6 +21,9 @@ struct mc_network {
   std::vector<mc::RxPar> par_h;
   void *side_d = nullptr;
   void *par_d = nullptr;
+  void *csr_d = nullptr;          // csr_ptr[S+1] then csr_ent[...]
+  void *exptab_d = nullptr;       // 2^(j/64), j = 0..63
+  int csr_len = 0;
 };
 
 namespace mc {
@@ -43,6 +46,7 @@ struct Tuned {
   int variant;        // MC_VARIANT_PLAIN or MC_VARIANT_PERSISTENT
   int threads;        // threads per block
   int blocks_per_sm;  // persistent grid size per SM
+  int strag_steps;    // attempts before a persistent lane hands its cell off (<= 0: never)
 };
 Tuned autotune_pick(const mc_network *net, const mc_burn_opts &o);
 
@@ -50,6 +54,10 @@ Tuned autotune_pick(const mc_network *net, const mc_burn_opts &o);
 // precision LT; defined in mc_launch.cuh, instantiated in mc_inst_<N>.cu.
 template <int N, typename LT>
 mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int variant, int threads,
-                     int blocks_per_sm, unsigned long long *next, cudaStream_t st);
+                     int blocks_per_sm, int strag_steps, unsigned long long *next, cudaStream_t st);
+
+// Library-owned record buffer for straggler hand-off (grown on demand) and its
+// claim counter, on the current device.
+mc_status straggler_scratch(size_t bytes, void **rec, uint32_t **count);
 
 }  // namespace mc

@@ -43,6 +43,9 @@ __device__ void load_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a, in
   L.cell = c;
   L.status = CELL_OK;
   L.q = 0;
+  L.kept = false;
+  L.todo = TD_NONE;
+  L.eta_pend = 1.0;
 #pragma unroll
   for (int k = 0; k < NSTAT; ++k) L.st[k] = 0;
   bool good = true;
@@ -116,7 +119,7 @@ __device__ void store_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a) {
 }
 
 template <int N, typename LT>
-__global__ void __launch_bounds__(128) k_burn_plain(DNet net, Opts o, CellArgs a) {
+__global__ void __launch_bounds__(256) k_burn_plain(DNet net, Opts o, CellArgs a) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= count_of(a)) return;
   Lane<N, LT> L;
@@ -124,15 +127,28 @@ __global__ void __launch_bounds__(128) k_burn_plain(DNet net, Opts o, CellArgs a
   while (L.phase != PH_DONE) {
     const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
     advance(L, net, o, ok);
+    run_stages(L, net, o);
   }
   store_cell(L, net, a);
 }
 
-// Persistent worker. `next` counts cells handed out (reset to 0 before the
-// launch). Every lane of every warp runs the loop, so warp-wide votes are safe.
+// Straggler hand-off: a cell still running after `threshold` step attempts is
+// written (whole lane state, at the start of an attempt) to record k of `rec`
+// and finished later by the warp-cooperative kernel; the lane takes a new cell.
+struct StragArgs {
+  void *rec;           // nullptr: no hand-off
+  uint32_t *count;     // records claimed (may exceed cap; only cap are written)
+  uint32_t cap;
+  int threshold;
+};
+
+// Persistent worker loop over one queue of cells. `next` counts cells handed
+// out (reset to 0 before the launch). Every lane of the warp runs the loop, so
+// the warp-wide votes are safe; the loop returns once the queue is drained and
+// every lane's cell is stored or handed off.
 template <int N, typename LT>
-__global__ void __launch_bounds__(128) k_burn_persistent(DNet net, Opts o, CellArgs a,
-                                                         unsigned long long *next) {
+__device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs &a,
+                                  unsigned long long *next, const StragArgs &sa) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t total = count_of(a);
@@ -161,6 +177,55 @@ __global__ void __launch_bounds__(128) k_burn_persistent(DNet net, Opts o, CellA
     if (L.phase != PH_IDLE && L.phase != PH_DONE) {
       const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
       advance(L, net, o, ok);
+      run_stages(L, net, o);
+      if (sa.rec && L.phase == PH_NEWTON && L.m == 0 && L.attempts >= sa.threshold && !L.kept) {
+        const uint32_t k = atomicAdd(sa.count, 1u);
+        if (k < sa.cap) {
+          static_cast<Lane<N, LT> *>(sa.rec)[k] = L;
+          L.phase = PH_IDLE;
+        } else {
+          L.kept = true;
+        }
+      }
+    }
+  }
+}
+
+template <int N, typename LT>
+__global__ void __launch_bounds__(256) k_burn_persistent(DNet net, Opts o, CellArgs a,
+                                                         unsigned long long *next, StragArgs sa) {
+  persistent_worker<N, LT>(net, o, a, next, sa);
+}
+
+// One segment of a mixed launch: a network, its cells and its compiled bucket.
+struct SegDev {
+  DNet net;
+  CellArgs a;
+  int bucket;
+};
+
+constexpr int MIXED_MAX_SEGS = 8;
+
+struct MixedArgs {
+  SegDev seg[MIXED_MAX_SEGS];
+  int nseg;
+};
+
+// Mixed persistent launch: every warp drains the segment queues starting at a
+// segment chosen by its warp index, so all networks start at once and warps
+// that finish one network move on to the next (one launch for all networks).
+template <typename LT>
+__global__ void __launch_bounds__(256) k_burn_mixed(MixedArgs m, Opts o, unsigned long long *next) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const StragArgs sa{nullptr, nullptr, 0u, 0};
+  for (int s0 = 0; s0 < m.nseg; ++s0) {
+    const int s = (s0 + warp) % m.nseg;
+    const SegDev &g = m.seg[s];
+    switch (g.bucket) {
+      case 3: persistent_worker<3, LT>(g.net, o, g.a, next + s, sa); break;
+      case 13: persistent_worker<13, LT>(g.net, o, g.a, next + s, sa); break;
+      case 33: persistent_worker<33, LT>(g.net, o, g.a, next + s, sa); break;
+      default: persistent_worker<40, LT>(g.net, o, g.a, next + s, sa); break;
     }
   }
 }

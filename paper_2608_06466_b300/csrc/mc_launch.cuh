@@ -6,13 +6,13 @@
 #include <algorithm>
 
 #include "mc_internal.h"
-#include "mc_kernels.cuh"
+#include "mc_warp.cuh"
 
 namespace mc {
 
 template <int N, typename LT>
 mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int variant, int threads,
-                     int blocks_per_sm, unsigned long long *next, cudaStream_t st) {
+                     int blocks_per_sm, int strag_steps, unsigned long long *next, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -27,7 +27,40 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
     int64_t blocks = (int64_t)sms * blocks_per_sm;
     if (!a.n_dev) blocks = std::min<int64_t>(blocks, (a.n_cells + threads - 1) / threads);
     if (blocks < 1) blocks = 1;
-    k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next);
+    StragArgs sa{nullptr, nullptr, 0u, 0};
+    const int64_t ncap = a.n_dev ? 0 : std::min<int64_t>(16384, std::max<int64_t>(256, a.n_cells / 64));
+    if (strag_steps > 0 && ncap > 0 && strag_steps < o.max_steps) {
+      void *rec = nullptr;
+      uint32_t *cnt = nullptr;
+      mc_status s = straggler_scratch(sizeof(Lane<N, LT>) * (size_t)ncap, &rec, &cnt);
+      if (s != MC_OK) return s;
+      sa = StragArgs{rec, cnt, (uint32_t)ncap, strag_steps};
+      e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
+      if (e != cudaSuccess) return cuda_error(e, "straggler counter reset");
+    }
+    k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
+    if (sa.rec) {
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_error(e, "burn kernel launch");
+      count_launch(1);
+      // warp-cooperative pass over the handed-off cells (count read on the device)
+      // one-warp blocks, 8 per SM: each straggler gets its own warp and at most
+      // two share an SM sub-partition's FP64 pipe
+      const int per_warp = (int)wsh_bytes<N, LT>(d.R);
+      const int wthreads = 32;
+      const int smem = per_warp;
+      static thread_local int configured = 0;
+      if (configured < smem) {
+        e = cudaFuncSetAttribute(k_burn_straggler<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return cuda_error(e, "straggler smem attribute");
+        configured = smem;
+      }
+      e = cudaMemsetAsync(next + 1, 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return cuda_error(e, "straggler queue reset");
+      const int wblocks = std::max(1, std::min(sms * 8, (int)sa.cap));
+      k_burn_straggler<N, LT><<<wblocks, wthreads, smem, st>>>(d, o, a, (const Lane<N, LT> *)sa.rec, sa.count,
+                                                              sa.cap, next + 1, per_warp);
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "burn kernel launch");

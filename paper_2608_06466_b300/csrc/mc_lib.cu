@@ -53,6 +53,7 @@ extern "C" void mc_burn_opts_default(mc_burn_opts *o) {
   o->variant = MC_VARIANT_AUTO;
   o->block_threads = 0;
   o->blocks_per_sm = 0;
+  o->straggler_steps = 0;
 }
 
 // ---------------------------------------------------------------- networks
@@ -106,9 +107,33 @@ extern "C" mc_status mc_network_create(const mc_network_desc *d, mc_network **ou
   if (e == cudaSuccess) e = cudaMalloc(&net->par_d, sizeof(RxPar) * par.size());
   if (e == cudaSuccess) e = cudaMemcpy(net->side_d, side.data(), sizeof(int4) * side.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(net->par_d, par.data(), sizeof(RxPar) * par.size(), cudaMemcpyHostToDevice);
+  // occurrence lists in the order the right-hand side scatters: per reaction
+  // reactant 0, product 0, reactant 1, product 1
+  std::vector<std::vector<int>> occ(S);
+  for (int r = 0; r < R; ++r) {
+    const int4 q = side[r];
+    const int sp[4] = {q.x, q.z, q.y, q.w};
+    const int slot[4] = {0, 2, 1, 3};
+    for (int k = 0; k < 4; ++k)
+      if (sp[k] >= 0) occ[sp[k]].push_back(4 * r + slot[k]);
+  }
+  std::vector<int> csr(S + 1);
+  csr[0] = 0;
+  for (int i = 0; i < S; ++i) csr[i + 1] = csr[i] + (int)occ[i].size();
+  for (int i = 0; i < S; ++i) csr.insert(csr.end(), occ[i].begin(), occ[i].end());
+  net->csr_len = (int)csr.size();
+  // 2^(j/64) for the table-driven exponential, rounded once from extended precision
+  double tab[64];
+  for (int j = 0; j < 64; ++j) tab[j] = (double)exp2l((long double)j / 64.0L);
+  if (e == cudaSuccess) e = cudaMalloc(&net->exptab_d, sizeof tab);
+  if (e == cudaSuccess) e = cudaMemcpy(net->exptab_d, tab, sizeof tab, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&net->csr_d, sizeof(int) * csr.size());
+  if (e == cudaSuccess) e = cudaMemcpy(net->csr_d, csr.data(), sizeof(int) * csr.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(net->side_d);
     cudaFree(net->par_d);
+    cudaFree(net->csr_d);
+    cudaFree(net->exptab_d);
     delete net;
     return cuda_error(e, "mc_network_create upload");
   }
@@ -120,6 +145,8 @@ extern "C" mc_status mc_network_destroy(mc_network *net) {
   if (!net) return MC_OK;
   cudaFree(net->side_d);
   cudaFree(net->par_d);
+  cudaFree(net->csr_d);
+  cudaFree(net->exptab_d);
   delete net;
   return MC_OK;
 }
@@ -135,6 +162,9 @@ DNet mc::dnet_of(const mc_network *net) {
   d.gm1 = net->gamma - 1.0;
   d.side = (const int4 *)net->side_d;
   d.par = (const RxPar *)net->par_d;
+  d.csr_ptr = (const int *)net->csr_d;
+  d.csr_ent = (const int *)net->csr_d + (net->S + 1);
+  d.exptab = (const double *)net->exptab_d;
   return d;
 }
 
@@ -143,9 +173,9 @@ DNet mc::dnet_of(const mc_network *net) {
 // FP32 pass's retry list (grown on demand, never shrunk).
 namespace {
 struct DevScratch {
-  unsigned long long *next = nullptr;   // [MAX_QUEUES]
-  uint32_t *retry_count = nullptr;
-  int32_t *retry = nullptr;
+  unsigned long long *next = nullptr;   // [MAX_QUEUES] queue counters
+  uint32_t *retry_count = nullptr;      // [MAX_QUEUES] retry-list lengths
+  int32_t *retry = nullptr;             // retry lists (cells)
   int64_t retry_cap = 0;
 };
 std::mutex g_scratch_mu;
@@ -159,7 +189,7 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
   DevScratch &s = g_scratch[dev];
   cudaError_t e;
   if (!s.next) {
-    e = cudaMalloc(&s.next, sizeof(unsigned long long) * MAX_QUEUES + sizeof(uint32_t) * 4);
+    e = cudaMalloc(&s.next, (sizeof(unsigned long long) + sizeof(uint32_t)) * MAX_QUEUES);
     if (e != cudaSuccess) return cuda_error(e, "scratch allocation");
     s.retry_count = (uint32_t *)(s.next + MAX_QUEUES);
   }
@@ -182,22 +212,59 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
   return MC_OK;
 }
 
+namespace {
+struct StragScratch {
+  void *rec = nullptr;
+  uint32_t *count = nullptr;
+  size_t bytes = 0;
+};
+StragScratch g_strag[64];
+}  // namespace
+
+mc_status mc::straggler_scratch(size_t bytes, void **rec, uint32_t **count) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return set_error(MC_E_INVALID, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  StragScratch &s = g_strag[dev];
+  cudaError_t e;
+  if (!s.count) {
+    e = cudaMalloc(&s.count, 256);
+    if (e != cudaSuccess) return cuda_error(e, "straggler counter allocation");
+  }
+  if (bytes > s.bytes) {
+    if (s.rec) {
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_error(e, "straggler grow sync");
+      cudaFree(s.rec);
+      s.rec = nullptr;
+      s.bytes = 0;
+    }
+    e = cudaMalloc(&s.rec, bytes);
+    if (e != cudaSuccess) return cuda_error(e, "straggler record allocation");
+    s.bytes = bytes;
+  }
+  *rec = s.rec;
+  *count = s.count;
+  return MC_OK;
+}
+
 // ---------------------------------------------------------------- launches
 namespace {
 
 template <typename LT>
 mc_status dispatch(const mc_network *net, const DNet &d, const Opts &o, const CellArgs &a,
-                   int variant, int threads, int bps, unsigned long long *next, cudaStream_t st) {
+                   int variant, int threads, int bps, int strag, unsigned long long *next, cudaStream_t st) {
   switch (net->n) {
-    case 3: return launch_one<3, LT>(d, o, a, variant, threads, bps, next, st);
-    case 13: return launch_one<13, LT>(d, o, a, variant, threads, bps, next, st);
-    case 33: return launch_one<33, LT>(d, o, a, variant, threads, bps, next, st);
+    case 3: return launch_one<3, LT>(d, o, a, variant, threads, bps, strag, next, st);
+    case 13: return launch_one<13, LT>(d, o, a, variant, threads, bps, strag, next, st);
+    case 33: return launch_one<33, LT>(d, o, a, variant, threads, bps, strag, next, st);
     default: break;
   }
-  if (net->n <= 8) return launch_one<8, LT>(d, o, a, variant, threads, bps, next, st);
-  if (net->n <= 16) return launch_one<16, LT>(d, o, a, variant, threads, bps, next, st);
-  if (net->n <= 24) return launch_one<24, LT>(d, o, a, variant, threads, bps, next, st);
-  return launch_one<NMAX_ODE, LT>(d, o, a, variant, threads, bps, next, st);
+  if (net->n <= 8) return launch_one<8, LT>(d, o, a, variant, threads, bps, strag, next, st);
+  if (net->n <= 16) return launch_one<16, LT>(d, o, a, variant, threads, bps, strag, next, st);
+  if (net->n <= 24) return launch_one<24, LT>(d, o, a, variant, threads, bps, strag, next, st);
+  return launch_one<NMAX_ODE, LT>(d, o, a, variant, threads, bps, strag, next, st);
 }
 
 bool is_device_ptr(const void *p) {
@@ -225,6 +292,7 @@ mc_status mc::check_opts(const mc_burn_opts *opts, mc_burn_opts *o) {
   if (o->block_threads < 0 || o->block_threads > 1024 || (o->block_threads % 32) != 0)
     return set_error(MC_E_INVALID, "block_threads must be a multiple of 32 up to 1024");
   if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) return set_error(MC_E_INVALID, "blocks_per_sm must be 0..32");
+  if (o->straggler_steps < -1) return set_error(MC_E_INVALID, "straggler_steps must be -1, 0 or positive");
   return MC_OK;
 }
 
@@ -243,20 +311,20 @@ mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const C
   mc_status s = scratch_get(dev, ob.lu_precision == 32 ? a0.n_cells : 0, &next, &rcount, &retry);
   if (s != MC_OK) return s;
   if (ob.lu_precision == 64)
-    return dispatch<double>(net, d, o, a0, tu.variant, tu.threads, tu.blocks_per_sm, next, st);
+    return dispatch<double>(net, d, o, a0, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);
   CellArgs a = a0;
   a.retry = retry;
   a.retry_count = rcount;
   cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_error(e, "retry counter reset");
-  s = dispatch<float>(net, d, o, a, tu.variant, tu.threads, tu.blocks_per_sm, next, st);
+  s = dispatch<float>(net, d, o, a, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);
   if (s != MC_OK) return s;
   // FP64 pass over the list; its length is read on the device
   CellArgs b = a0;
   b.index = retry;
   b.n_dev = rcount;
   b.n_cells = a0.n_cells;
-  return dispatch<double>(net, d, o, b, MC_VARIANT_PERSISTENT, tu.threads, tu.blocks_per_sm, next, st);
+  return dispatch<double>(net, d, o, b, MC_VARIANT_PERSISTENT, tu.threads, tu.blocks_per_sm, 0, next, st);
 }
 
 extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,

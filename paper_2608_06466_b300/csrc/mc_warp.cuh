@@ -1,0 +1,805 @@
+// mc_warp.cuh -- warp-cooperative form of the same integrator, for cells that
+// need far more steps than the rest (stragglers).
+//
+// On this GPU an FP64 warp instruction occupies the FP64 pipe for the whole
+// warp whether 1 or 32 lanes are active, so a long cell left alone on one lane
+// pays full-warp price for every operation of every step. Here the whole warp
+// advances ONE cell: vector components live one per lane (component i on lane
+// i mod 32, slot i / 32), the reaction rates of a right-hand side are spread
+// over the lanes, per-species sums follow the network's occurrence lists, the
+// iteration matrix sits in shared memory and is factored row-parallel, and
+// scalars are replicated so every lane takes the same branch. The decisions
+// are the thread form's (same rules, same constants); only the order of a few
+// floating-point reductions differs.
+#pragma once
+
+#include "mc_kernels.cuh"
+
+namespace mc {
+
+constexpr unsigned WFULL = 0xffffffffu;
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(WFULL, v, o);
+  return v;
+}
+
+// per-warp shared workspace (carved from dynamic shared memory)
+template <typename LT>
+struct WSh {
+  LT *J;            // [N*N] Jacobian, row stride N
+  LT *P;            // [N*N] factored iteration matrix
+  unsigned char *piv;
+  double *yb;       // [N]   point of the right-hand side, for broadcast
+  double *wb;       // [R]   net reaction rates
+  double *dw;       // [5R]  d w / d x per side slot, then d w / d T
+};
+
+template <int N, typename LT>
+__host__ __device__ inline size_t wsh_bytes(int R) {
+  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  return al(sizeof(LT) * N * N) * 2 + al(N) + al(sizeof(double) * N) + al(sizeof(double) * (R > 0 ? R : 1)) +
+         al(sizeof(double) * 5 * (R > 0 ? R : 1));
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ WSh<LT> wsh_carve(unsigned char *p, int R) {
+  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  WSh<LT> s;
+  s.J = (LT *)p;
+  p += al(sizeof(LT) * N * N);
+  s.P = (LT *)p;
+  p += al(sizeof(LT) * N * N);
+  s.piv = p;
+  p += al(N);
+  s.yb = (double *)p;
+  p += al(sizeof(double) * N);
+  s.wb = (double *)p;
+  p += al(sizeof(double) * (R > 0 ? R : 1));
+  s.dw = (double *)p;
+  return s;
+}
+
+// register state of the warp's cell (vector slots: component lane + 32 s)
+template <int N>
+struct WState {
+  static constexpr int NS = (N + 31) / 32;
+  double z[QMAX + 2][NS];
+  double e[NS], es[NS], iw[NS], y[NS], f[NS];
+  double l[QMAX + 1];
+  double hist[QMAX + 3];
+  double t, h, tend, crate, gamma_p, gamma, cq, esave_h, delp, eta_max, h0;
+  CellIn cin;
+  int64_t cell;
+  int q, qwait, nef, ncf, jage, page, attempts, m, phase, status;
+  bool need_j, need_p, jcur, have_es, last;
+  int st[NSTAT];
+};
+
+__device__ __forceinline__ int wlane() { return threadIdx.x & 31; }
+
+// value of distributed component c (all lanes receive it)
+template <int NS>
+__device__ __forceinline__ double wget(const double (&v)[NS], int c) {
+  double x = v[0];
+  if (NS > 1 && c >= 32) x = v[NS - 1];
+  return __shfl_sync(WFULL, x, c & 31);
+}
+
+template <int N>
+__device__ __forceinline__ double w_wrms(int n, const double (&v)[WState<N>::NS], const double (&iw)[WState<N>::NS]) {
+  constexpr int NS = WState<N>::NS;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int i = wlane() + 32 * k;
+    if (i < n) {
+      const double r = v[k] * iw[k];
+      s += r * r;
+    }
+  }
+  return sqrt(wsum(s) / n);
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void w_load(WState<N> &W, const Lane<N, LT> &L, const WSh<LT> &sh, const DNet &net) {
+  constexpr int NS = WState<N>::NS;
+  const int n = net.n, ln = wlane();
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int i = ln + 32 * k;
+    const bool in = i < n;
+    for (int j = 0; j < QMAX + 2; ++j) W.z[j][k] = in ? L.z[j][in ? i : 0] : 0.0;
+    W.e[k] = in ? L.e[in ? i : 0] : 0.0;
+    W.es[k] = in ? L.es[in ? i : 0] : 0.0;
+    W.iw[k] = in ? L.iw[in ? i : 0] : 0.0;
+    W.y[k] = in ? L.y[in ? i : 0] : 0.0;
+    W.f[k] = 0.0;
+  }
+  for (int idx = ln; idx < n * N; idx += 32) {
+    sh.J[idx] = L.J[idx];
+    sh.P[idx] = L.P[idx];
+  }
+  for (int i = ln; i < n; i += 32) sh.piv[i] = L.piv[i];
+  for (int k = 0; k <= QMAX; ++k) W.l[k] = L.l[k];
+  for (int k = 0; k < QMAX + 3; ++k) W.hist[k] = L.hist[k];
+  W.t = L.t; W.h = L.h; W.tend = L.tend; W.crate = L.crate; W.gamma_p = L.gamma_p; W.gamma = L.gamma;
+  W.cq = L.cq; W.esave_h = L.esave_h; W.delp = L.delp; W.eta_max = L.eta_max; W.h0 = L.h0;
+  W.cin = L.cin; W.cell = L.cell;
+  W.q = L.q; W.qwait = L.qwait; W.nef = L.nef; W.ncf = L.ncf; W.jage = L.jage; W.page = L.page;
+  W.attempts = L.attempts; W.m = L.m; W.phase = L.phase; W.status = L.status;
+  W.need_j = L.need_j; W.need_p = L.need_p; W.jcur = L.jcur; W.have_es = L.have_es; W.last = L.last;
+  for (int k = 0; k < NSTAT; ++k) W.st[k] = L.st[k];
+  __syncwarp();
+}
+
+// temperature quantities of the point in sh.yb (energy form) or of the cell
+__device__ __forceinline__ bool w_temperature(const DNet &net, const CellIn &c, const double *yb, double &T,
+                                              double &X, double &lnT, double &invT) {
+  lnT = c.lnT;
+  invT = c.invT;
+  T = 0.0;
+  X = 0.0;
+  if (!net.energy) return true;
+  double xs = 0.0;
+  for (int i = wlane(); i < net.S; i += 32) xs += yb[i];
+  X = wsum(xs);
+  T = net.gm1 * yb[net.S] / (KB_EV * X);
+  if (!(T > 0.0) || !isfinite(T)) return false;
+  lnT = log(T);
+  invT = 1.0 / T;
+  return true;
+}
+
+// Right-hand side at W.y into W.f; returns false (uniformly) when it cannot be evaluated.
+template <int N, typename LT>
+__device__ __forceinline__ bool w_rhs(WState<N> &W, const WSh<LT> &sh, const DNet &net) {
+  constexpr int NS = WState<N>::NS;
+  const int n = net.n, S = net.S, ln = wlane();
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int i = ln + 32 * k;
+    if (i < n) sh.yb[i] = W.y[k];
+  }
+  __syncwarp();
+  double T, X, lnT, invT;
+  if (!w_temperature(net, W.cin, sh.yb, T, X, lnT, invT)) return false;
+  const CellIn &c = W.cin;
+  double epart = 0.0;
+  for (int r = ln; r < net.R; r += 32) {
+    const int4 s = __ldg(&net.side[r]);
+    const RxPar &p = net.par[r];
+    double kf = rexp(__ldg(&p.lnAf) + __ldg(&p.bf) * lnT - __ldg(&p.Cf) * invT, net.exptab);
+    double kr = 0.0;
+    if (__ldg(&p.rev) != 0.0) kr = rexp(__ldg(&p.lnAr) + __ldg(&p.br) * lnT - __ldg(&p.Cr) * invT, net.exptab);
+    if (c.ks) {
+      const double sc = c.ks[r * c.ks_ld];
+      kf *= sc;
+      kr *= sc;
+    }
+    const double pf = (s.y < 0) ? sh.yb[s.x] : c.nd * sh.yb[s.x] * sh.yb[s.y];
+    const double pr = (s.w < 0) ? sh.yb[s.z] : c.nd * sh.yb[s.z] * sh.yb[s.w];
+    const double w = kf * pf - kr * pr;
+    sh.wb[r] = w;
+    if (net.energy) epart += __ldg(&p.dE) * w;
+  }
+  __syncwarp();
+  const double fu = net.energy ? wsum(epart) : 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int i = ln + 32 * k;
+    double v = 0.0;
+    if (i < S) {
+      for (int q = __ldg(&net.csr_ptr[i]); q < __ldg(&net.csr_ptr[i + 1]); ++q) {
+        const int ent = __ldg(&net.csr_ent[q]);
+        const double w = sh.wb[ent >> 2];
+        v = ((ent & 3) < 2) ? v - w : v + w;
+      }
+    } else if (i == S && net.energy) {
+      v = fu;
+    }
+    W.f[k] = v;
+    if (i < n && !isfinite(v)) bad = true;
+  }
+  __syncwarp();
+  return !__any_sync(WFULL, bad);
+}
+
+// Analytic Jacobian at the point in sh.yb, into sh.J (same formulas as net_jac).
+template <int N, typename LT>
+__device__ __forceinline__ bool w_jac(WState<N> &W, const WSh<LT> &sh, const DNet &net) {
+  const int n = net.n, S = net.S, ln = wlane();
+  double T, X, lnT, invT;
+  if (!w_temperature(net, W.cin, sh.yb, T, X, lnT, invT)) return false;
+  const CellIn &c = W.cin;
+  double gpart = 0.0;
+  for (int r = ln; r < net.R; r += 32) {
+    const int4 s = __ldg(&net.side[r]);
+    const RxPar &p = net.par[r];
+    const double bf = __ldg(&p.bf), Cf = __ldg(&p.Cf);
+    double kf = rexp(__ldg(&p.lnAf) + bf * lnT - Cf * invT, net.exptab);
+    double kr = 0.0, br = 0.0, Cr = 0.0;
+    if (__ldg(&p.rev) != 0.0) {
+      br = __ldg(&p.br);
+      Cr = __ldg(&p.Cr);
+      kr = rexp(__ldg(&p.lnAr) + br * lnT - Cr * invT, net.exptab);
+    }
+    if (c.ks) {
+      const double sc = c.ks[r * c.ks_ld];
+      kf *= sc;
+      kr *= sc;
+    }
+    double *d = sh.dw + 5 * r;
+    double pf, pr;
+    if (s.y < 0) { pf = sh.yb[s.x]; d[0] = kf; d[1] = 0.0; }
+    else { pf = c.nd * sh.yb[s.x] * sh.yb[s.y]; d[0] = kf * (c.nd * sh.yb[s.y]); d[1] = kf * (c.nd * sh.yb[s.x]); }
+    if (s.w < 0) { pr = sh.yb[s.z]; d[2] = -kr; d[3] = 0.0; }
+    else { pr = c.nd * sh.yb[s.z] * sh.yb[s.w]; d[2] = -kr * (c.nd * sh.yb[s.w]); d[3] = -kr * (c.nd * sh.yb[s.z]); }
+    d[4] = kf * (bf + Cf * invT) * invT * pf - kr * (br + Cr * invT) * invT * pr;
+    if (net.energy) gpart += __ldg(&p.dE) * d[4];
+  }
+  __syncwarp();
+  const double gS = net.energy ? wsum(gpart) : 0.0;
+  for (int idx = ln; idx < n * N; idx += 32) sh.J[idx] = (LT)0;
+  __syncwarp();
+  bool bad = false;
+  // species rows: lane i assembles row i from the reactions species i takes part in
+  for (int i = ln; i < n; i += 32) {
+    double g = 0.0;
+    if (i < S) {
+      for (int q = __ldg(&net.csr_ptr[i]); q < __ldg(&net.csr_ptr[i + 1]); ++q) {
+        const int ent = __ldg(&net.csr_ent[q]);
+        const int r = ent >> 2;
+        const double sgn = ((ent & 3) < 2) ? -1.0 : 1.0;
+        const int4 s = __ldg(&net.side[r]);
+        const int col[4] = {s.x, s.y, s.z, s.w};
+        const double *d = sh.dw + 5 * r;
+        g += sgn * d[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (col[b] >= 0) sh.J[i * N + col[b]] += (LT)(sgn * d[b]);
+      }
+    } else {
+      g = gS;
+    }
+    if (net.energy) {
+      const double dTdx = -T / X, dTdu = net.gm1 / (KB_EV * X);
+      if (i == S) {
+        // energy row: column j collects dE_r d w_r / d x_j over species j's slots
+        for (int j = 0; j < S; ++j) {
+          double acc = 0.0;
+          for (int q = __ldg(&net.csr_ptr[j]); q < __ldg(&net.csr_ptr[j + 1]); ++q) {
+            const int ent = __ldg(&net.csr_ent[q]);
+            acc += __ldg(&net.par[ent >> 2].dE) * sh.dw[5 * (ent >> 2) + (ent & 3)];
+          }
+          sh.J[S * N + j] += (LT)acc;
+        }
+      }
+      const LT gx = (LT)(g * dTdx);
+      for (int j = 0; j < S; ++j) sh.J[i * N + j] += gx;
+      sh.J[i * N + S] += (LT)(g * dTdu);
+    }
+    for (int j = 0; j < n; ++j)
+      if (!isfinite((double)sh.J[i * N + j])) bad = true;
+  }
+  __syncwarp();
+  return !__any_sync(WFULL, bad);
+}
+
+// Row-parallel LU with partial pivoting in shared memory (first maximal |a|).
+template <int N, typename LT>
+__device__ __forceinline__ bool w_lu(const WSh<LT> &sh, int n) {
+  const int ln = wlane();
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + ln; i < n; i += 32) {
+      const double v = fabs((double)sh.P[i * N + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(WFULL, best, o);
+      const int oi = __shfl_xor_sync(WFULL, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (ln == 0) sh.piv[k] = (unsigned char)bi;
+    if (!(best > 0.0)) { __syncwarp(); return false; }
+    if (bi != k)
+      for (int j = ln; j < n; j += 32) {
+        const LT tmp = sh.P[k * N + j];
+        sh.P[k * N + j] = sh.P[bi * N + j];
+        sh.P[bi * N + j] = tmp;
+      }
+    __syncwarp();
+    const LT inv = (LT)1 / sh.P[k * N + k];
+    for (int i = k + 1 + ln; i < n; i += 32) {
+      const LT m = sh.P[i * N + k] * inv;
+      sh.P[i * N + k] = m;
+      for (int j = k + 1; j < n; ++j) sh.P[i * N + j] -= m * sh.P[k * N + j];
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// Solve (LU) x = P d for the distributed vector d (in place), in precision LT.
+template <int N, typename LT>
+__device__ __forceinline__ void w_solve(const WSh<LT> &sh, int n, double (&d)[WState<N>::NS]) {
+  constexpr int NS = WState<N>::NS;
+  const int ln = wlane();
+  LT b[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) b[k] = (LT)d[k];
+  auto get = [&](int c) -> LT {
+    LT x = b[0];
+    if (NS > 1 && c >= 32) x = b[NS - 1];
+    return __shfl_sync(WFULL, x, c & 31);
+  };
+  auto put = [&](int c, LT v) {
+    if ((c & 31) == ln) {
+      if (NS > 1 && c >= 32) b[NS - 1] = v;
+      else b[0] = v;
+    }
+  };
+  for (int k = 0; k < n; ++k) {
+    const int p = sh.piv[k];
+    if (p != k) {
+      const LT vk = get(k), vp = get(p);
+      put(k, vp);
+      put(p, vk);
+    }
+  }
+  for (int j = 0; j < n; ++j) {
+    const LT bj = get(j);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int i = ln + 32 * k;
+      if (i > j && i < n) b[k] -= sh.P[i * N + j] * bj;
+    }
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    LT bj = get(j);
+    bj = bj / sh.P[j * N + j];
+    put(j, bj);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int i = ln + 32 * k;
+      if (i < j) b[k] -= sh.P[i * N + j] * bj;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) d[k] = (double)b[k];
+}
+
+// ---- step logic (mirrors the thread form in mc_device.cuh) -----------------
+template <int N>
+__device__ __forceinline__ void w_rescale(WState<N> &W, int n, double eta) {
+  constexpr int NS = WState<N>::NS;
+  double r = 1.0;
+#pragma unroll
+  for (int j = 1; j <= QMAX + 1; ++j) {
+    if (j <= W.q) {
+      r *= eta;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) W.z[j][k] *= r;
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void w_predict(WState<N> &W) {
+  constexpr int NS = WState<N>::NS;
+  const int q = W.q;
+#pragma unroll
+  for (int k = 0; k < QMAX; ++k)
+#pragma unroll
+    for (int j = QMAX; j > k; --j)
+      if (k < q && j <= q)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) W.z[j - 1][s] += W.z[j][s];
+}
+
+template <int N>
+__device__ __forceinline__ void w_retract(WState<N> &W) {
+  constexpr int NS = WState<N>::NS;
+  const int q = W.q;
+#pragma unroll
+  for (int k = QMAX - 1; k >= 0; --k)
+#pragma unroll
+    for (int j = k + 1; j <= QMAX; ++j)
+      if (k < q && j <= q)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) W.z[j - 1][s] -= W.z[j][s];
+}
+
+template <int N>
+__device__ __forceinline__ void w_begin_step(WState<N> &W, const DNet &net, const Opts &o) {
+  constexpr int NS = WState<N>::NS;
+  const int n = net.n, ln = wlane();
+  if (!(W.t < W.tend)) { W.status = CELL_OK; W.phase = PH_DONE; return; }
+  if (W.attempts >= o.max_steps) { W.status = CELL_MAX_STEPS; W.phase = PH_DONE; return; }
+  W.last = false;
+  if (W.t + W.h >= W.tend) {
+    const double hn = W.tend - W.t;
+    w_rescale(W, n, hn / W.h);
+    W.h = hn;
+    W.last = true;
+  }
+  W.attempts += 1;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int i = ln + 32 * k;
+    W.iw[k] = (i < n) ? 1.0 / (o.rtol * fabs(W.z[0][k]) + o.atol) : 0.0;
+  }
+  w_predict(W);
+  const int q = W.q;
+  double gaps[QMAX + 2], xi[QMAX + 2];
+  gaps[0] = W.h;
+#pragma unroll
+  for (int k = 0; k < QMAX + 1; ++k) gaps[k + 1] = W.hist[k];
+  xi_of(W.h, gaps, q + 1, xi);
+#pragma unroll
+  for (int k = 0; k <= QMAX; ++k) W.l[k] = 0.0;
+  W.l[0] = 1.0;
+#pragma unroll
+  for (int j = 1; j <= QMAX; ++j)
+    if (j <= q) {
+      const double c = 1.0 / xi[j - 1];
+#pragma unroll
+      for (int k = QMAX; k >= 1; --k)
+        if (k <= j) W.l[k] += c * W.l[k - 1];
+    }
+  double xq = xi[0];
+#pragma unroll
+  for (int j = 1; j <= QMAX; ++j)
+    if (j == q) xq = xi[j];
+  W.cq = (1.0 / xq) / W.l[1];
+  W.gamma = W.h / W.l[1];
+  W.jcur = false;
+  W.m = 0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    W.e[k] = 0.0;
+    W.y[k] = W.z[0][k];
+  }
+  W.phase = PH_NEWTON;
+}
+
+template <int N>
+__device__ __forceinline__ void w_conv_failure(WState<N> &W, const DNet &net, const Opts &o) {
+  w_retract(W);
+  W.ncf += 1;
+  W.st[ST_CONV_FAILS] += 1;
+  if (W.ncf >= MXNCF) { W.status = CELL_CONV_FAIL; W.phase = PH_DONE; return; }
+  w_rescale(W, net.n, ETACF);
+  W.h *= ETACF;
+  W.need_p = true;
+  W.qwait = W.q + 1;
+  W.have_es = false;
+  if (W.t + W.h == W.t) { W.status = CELL_H_UNDERFLOW; W.phase = PH_DONE; return; }
+  w_begin_step(W, net, o);
+}
+
+template <int N>
+__device__ __forceinline__ void w_lower_order(WState<N> &W, const double *xi) {
+  constexpr int NS = WState<N>::NS;
+  double c[QMAX + 2];
+  const int q = W.q;
+  shifted_product(q, xi, c);
+  double zq[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) zq[s] = 0.0;
+#pragma unroll
+  for (int j = 2; j <= QMAX; ++j)
+    if (j == q)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) zq[s] = W.z[j][s];
+#pragma unroll
+  for (int j = 1; j < QMAX; ++j)
+    if (j < q)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) W.z[j][s] -= c[j] * zq[s];
+  W.q = q - 1;
+}
+
+template <int N>
+__device__ __forceinline__ void w_after_convergence(WState<N> &W, const DNet &net, const Opts &o) {
+  constexpr int NS = WState<N>::NS;
+  const int n = net.n;
+  const int q = W.q;
+  const double dsm = W.cq * w_wrms<N>(n, W.e, W.iw);
+  double xi[QMAX + 2];
+  if (dsm > 1.0) {
+    w_retract(W);
+    W.nef += 1;
+    W.st[ST_ERR_FAILS] += 1;
+    W.have_es = false;
+    if (W.nef >= KFC) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) W.y[s] = W.z[0][s];
+      W.phase = PH_RESTART;
+      return;
+    }
+    double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
+    int qn = q;
+    if (q > 1) {
+      xi_of(W.h, W.hist, q, xi);
+      double prod = 1.0, l1 = 0.0;
+#pragma unroll
+      for (int j = 1; j <= QMAX; ++j)
+        if (j <= q - 1) {
+          prod *= xi[j - 1];
+          l1 += 1.0 / xi[j - 1];
+        }
+      double zq[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) zq[k] = 0.0;
+#pragma unroll
+      for (int j = 2; j <= QMAX; ++j)
+        if (j == q)
+#pragma unroll
+          for (int k = 0; k < NS; ++k) zq[k] = W.z[j][k];
+      const double est = (prod / l1) * w_wrms<N>(n, zq, W.iw);
+      const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
+      if (eta_m > eta) { eta = eta_m; qn = q - 1; }
+    }
+    eta = fmax(ETAMIN, fmin(eta, 1.0));
+    if (qn < q) w_lower_order(W, xi);
+    w_rescale(W, n, eta);
+    W.h *= eta;
+    W.qwait = W.q + 1;
+    if (W.t + W.h == W.t) { W.status = CELL_H_UNDERFLOW; W.phase = PH_DONE; return; }
+    w_begin_step(W, net, o);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j <= QMAX; ++j)
+    if (j <= q)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) W.z[j][s] += W.l[j] * W.e[s];
+  W.t = W.last ? W.tend : W.t + W.h;
+  for (int k = QMAX + 2; k > 0; --k) W.hist[k] = W.hist[k - 1];
+  W.hist[0] = W.h;
+  W.st[ST_STEPS] += 1;
+  W.nef = 0;
+  W.ncf = 0;
+  W.jage += 1;
+  W.page += 1;
+  W.qwait -= 1;
+  if (W.qwait == 1 && q < o.qmax) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) W.es[s] = W.e[s];
+    W.esave_h = W.h;
+    W.have_es = true;
+  }
+  if (W.last) { W.status = CELL_OK; W.phase = PH_DONE; return; }
+  if (W.qwait > 0) { w_begin_step(W, net, o); return; }
+  double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
+  int qn = q;
+  xi_of(W.h, W.hist, q + 1, xi);
+  if (q > 1) {
+    double prod = 1.0, l1 = 0.0;
+#pragma unroll
+    for (int j = 1; j <= QMAX; ++j)
+      if (j <= q - 1) {
+        prod *= xi[j - 1];
+        l1 += 1.0 / xi[j - 1];
+      }
+    double zq[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) zq[k] = 0.0;
+#pragma unroll
+    for (int j = 2; j <= QMAX; ++j)
+      if (j == q)
+#pragma unroll
+        for (int k = 0; k < NS; ++k) zq[k] = W.z[j][k];
+    const double est = (prod / l1) * w_wrms<N>(n, zq, W.iw);
+    const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
+    if (eta_m > eta) { eta = eta_m; qn = q - 1; }
+  }
+  if (q < o.qmax && W.have_es) {
+    const double r = pow(W.h / W.esave_h, (double)(q + 1));
+    double dv[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dv[s] = W.e[s] - r * W.es[s];
+    const double est = w_wrms<N>(n, dv, W.iw) / ((double)(q + 2) * harmonic(q + 1));
+    const double eta_p = 1.0 / (pow(BIAS_QP1 * est, 1.0 / (q + 2)) + ADDON);
+    if (eta_p > eta) { eta = eta_p; qn = q + 1; }
+  }
+  W.have_es = false;
+  if (eta < THRESH) {
+    W.qwait = 2;
+    w_begin_step(W, net, o);
+    return;
+  }
+  eta = fmin(eta, W.eta_max);
+  W.eta_max = ETAMX;
+  if (qn > q) {
+    double prod = 1.0, c[QMAX + 2];
+#pragma unroll
+    for (int j = 1; j <= QMAX + 1; ++j)
+      if (j <= q + 1) prod *= xi[j - 1];
+    const double C = 1.0 / prod;
+    shifted_product(q + 1, xi, c);
+#pragma unroll
+    for (int j = 2; j <= QMAX + 1; ++j)
+      if (j == q + 1)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) W.z[j][s] = 0.0;
+#pragma unroll
+    for (int j = 1; j <= QMAX + 1; ++j)
+      if (j <= q + 1)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) W.z[j][s] += c[j] * C * W.e[s];
+    W.q = q + 1;
+  } else if (qn < q) {
+    w_lower_order(W, xi);
+  }
+  w_rescale(W, n, eta);
+  W.h *= eta;
+  W.qwait = W.q + 1;
+  w_begin_step(W, net, o);
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, const DNet &net, bool ok) {
+  constexpr int NS = WState<N>::NS;
+  const int n = net.n, ln = wlane();
+  if (!ok) return 3;
+  W.st[ST_RHS] += 1;
+  if (W.m == 0) {
+    bool newp = false;
+    if (W.need_j || W.jage >= MSBJ) {
+      if (!w_jac<N, LT>(W, sh, net)) return 3;
+      W.st[ST_JAC] += 1;
+      W.jcur = true;
+      W.need_j = false;
+      W.jage = 0;
+      newp = true;
+    }
+    if (newp || W.need_p || W.page >= MSBP || fabs(W.gamma / W.gamma_p - 1.0) > CCMAX) {
+      const LT g = (LT)W.gamma;
+      for (int idx = ln; idx < n * N; idx += 32) {
+        const int i = idx / N, j = idx - i * N;
+        if (j < n) sh.P[idx] = (i == j ? (LT)1 : (LT)0) - g * sh.J[idx];
+      }
+      __syncwarp();
+      W.st[ST_LU] += 1;
+      W.gamma_p = W.gamma;
+      W.page = 0;
+      W.need_p = false;
+      W.crate = CRATE0;
+      if (!w_lu<N, LT>(sh, n)) {
+        W.need_p = true;
+        return 2;
+      }
+    }
+  }
+  double d[NS];
+  const double rl1 = W.l[1];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int i = ln + 32 * s;
+    d[s] = (i < n) ? (W.h * W.f[s] - W.z[1][s]) / rl1 - W.e[s] : 0.0;
+  }
+  w_solve<N, LT>(sh, n, d);
+  W.st[ST_NEWTON] += 1;
+  if (W.gamma != W.gamma_p) {
+    const double sc = 2.0 / (1.0 + W.gamma / W.gamma_p);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) d[s] *= sc;
+  }
+  const double del = w_wrms<N>(n, d, W.iw);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    W.e[s] += d[s];
+    W.y[s] = W.z[0][s] + W.e[s];
+  }
+  if (W.m > 0) W.crate = fmax(CRDOWN * W.crate, del / W.delp);
+  const double dcon = del * fmin(1.0, W.crate) * W.cq / CORTES;
+  if (dcon <= 1.0) return 1;
+  W.m += 1;
+  if (W.m == MAXCOR || (W.m >= 2 && del > RDIV * W.delp)) return 2;
+  W.delp = del;
+  return 0;
+}
+
+// Consume f(y) (only the phases a handed-off cell can be in).
+template <int N, typename LT>
+__device__ __forceinline__ void w_advance(WState<N> &W, const WSh<LT> &sh, const DNet &net, const Opts &o, bool ok) {
+  constexpr int NS = WState<N>::NS;
+  if (W.phase == PH_NEWTON) {
+    const int r = w_newton_iter<N, LT>(W, sh, net, ok);
+    if (r == 0) return;
+    if (r == 1) { w_after_convergence(W, net, o); return; }
+    if (r == 2 && !W.jcur) {
+      W.need_j = true;
+      W.m = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        W.e[s] = 0.0;
+        W.y[s] = W.z[0][s];
+      }
+      return;
+    }
+    w_conv_failure(W, net, o);
+    return;
+  }
+  if (W.phase == PH_RESTART) {
+    if (!ok) { W.status = CELL_NONFINITE; W.phase = PH_DONE; return; }
+    W.st[ST_RHS] += 1;
+    W.h *= ETAMIN;
+    W.q = 1;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) W.z[1][s] = W.h * W.f[s];
+    W.qwait = 2;
+    if (W.t + W.h == W.t) { W.status = CELL_H_UNDERFLOW; W.phase = PH_DONE; return; }
+    w_begin_step(W, net, o);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void w_store(WState<N> &W, const DNet &net, const CellArgs &a) {
+  constexpr int NS = WState<N>::NS;
+  const int64_t c = W.cell;
+  const int S = net.S, ln = wlane();
+  if (a.retry && (W.status == CELL_CONV_FAIL || W.status == CELL_H_UNDERFLOW)) {
+    if (ln == 0) {
+      const uint32_t k = atomicAdd(a.retry_count, 1u);
+      a.retry[k] = (int32_t)c;
+    }
+    __syncwarp();
+    return;
+  }
+  double xs = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int i = ln + 32 * s;
+    if (i < S) {
+      a.x[i * a.ld + c] = W.z[0][s];
+      xs += W.z[0][s];
+    }
+  }
+  const double X = wsum(xs);
+  if (net.energy) {
+    const double u = wget<NS>(W.z[0], S);
+    if (ln == 0) a.T[c] = net.gm1 * u / (KB_EV * X);
+  }
+  if (ln == 0) a.status[c] = W.status;
+  if (a.stats && ln < NSTAT) {
+    int v = 0;
+    for (int k = 0; k < NSTAT; ++k)
+      if (k == ln) v = (k == ST_ORDER) ? W.q : W.st[k];
+    a.stats[ln * a.ld + c] = v;
+  }
+  __syncwarp();
+}
+
+// Straggler kernel: each warp takes handed-off cells (records of the thread
+// form's state) until the list is done; count is read on the device.
+template <int N, typename LT>
+__global__ void __launch_bounds__(128) k_burn_straggler(DNet net, Opts o, CellArgs a, const Lane<N, LT> *rec,
+                                                        const uint32_t *count, uint32_t cap,
+                                                        unsigned long long *next, int smem_per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const WSh<LT> sh = wsh_carve<N, LT>(smem + (threadIdx.x >> 5) * (size_t)smem_per_warp, net.R);
+  const uint32_t total = min(*count, cap);
+  for (;;) {
+    unsigned long long k = 0;
+    if (wlane() == 0) k = atomicAdd(next, 1ull);
+    k = __shfl_sync(WFULL, k, 0);
+    if (k >= total) break;
+    WState<N> W;
+    w_load<N, LT>(W, rec[k], sh, net);
+    while (W.phase != PH_DONE) {
+      const bool ok = w_rhs<N, LT>(W, sh, net);
+      w_advance<N, LT>(W, sh, net, o, ok);
+    }
+    w_store<N>(W, net, a);
+  }
+}
+
+}  // namespace mc

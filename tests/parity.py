@@ -8,9 +8,14 @@ integration error, which at rtol = 1e-6 can exceed 1e-5 (the oracle compiled
 with and without FMA contraction differs that much on ~3 % of the 13-ODE
 cells). So each cell is classified by the oracle itself:
 
-  stable     the oracle's result moves by < 1e-8 (relative) when the inputs
-             move by 1e-13 (relative): the result is a well-defined function of
-             the inputs at this rounding level, and the CUDA path must match it:
+  stable     the oracle's result moves by < 1e-8 (relative) both when the
+             inputs move by a small relative amount (1e-13 for the FP64 path,
+             whose differences are roundoff; 1e-9 for the FP32-matrix path,
+             whose Newton iterates differ at ~1e-7 of a correction, i.e. ~1e-13
+             of the state, and may stop one iteration apart) and when the
+             oracle is recompiled with FMA contraction (its rounding twin): the
+             result is a well-defined function of the inputs at this level, and
+             the CUDA path must match it:
              |g - o| <= 1e-5 |o| + 10 atol (abundances), |g - o| <= 1e-5 |o| (T).
   sensitive  otherwise: several results are correct, and a single run's error
              against the true solution is random-like (the FMA-compiled oracle
@@ -22,7 +27,15 @@ cells). So each cell is classified by the oracle itself:
              + 1e-9, p90(e_g) <= 3 p90(e_o) + 1e-9.
 
 Statuses must agree except for cells whose oracle attempt count is within 1 %
-of the step cap."""
+of the step cap.
+
+The FP32-matrix form is held to a bar derived from its arithmetic instead:
+with an FP32 iteration matrix the Newton iterates differ from the FP64 ones,
+so the iteration may stop at a different point inside its convergence bound
+(CORTES = 0.1 of the local tolerance, ~1e-7 of the state per step); over a
+cell's history those differences add up like a global error. Stable cells must
+be within 1e-4 and at least 99 % of them within 1e-5; the per-result error
+against the FP64 oracle is reported."""
 from __future__ import annotations
 
 import numpy as np
@@ -32,24 +45,35 @@ STABLE_MOVE = 1e-8
 PERTURB = 1e-13
 
 
-def classify(onet, cells, dt, burn, index=None, **kw):
-    """Oracle result, the perturbed-input oracle result and the stability
-    mask; ``burn`` is oracle.burn."""
+def _agree(a, o):
+    move = np.abs(a[0] - o[0]) / (np.abs(o[0]) + 1e-4)
+    ok = (move < STABLE_MOVE).all(axis=0) & (a[2] == o[2])
+    if o[1] is not None:
+        ok &= np.abs(a[1] - o[1]) < STABLE_MOVE * np.abs(o[1])
+    return ok
+
+
+def classify(onet, cells, dt, burn, index=None, perturb=PERTURB, twin=True, **kw):
+    """Oracle result and the stability mask (see module doc); ``burn`` is
+    oracle.burn, ``onet`` its network. twin=True also runs the oracle's
+    FMA-contracted rounding twin where the host supports it."""
     o = burn(onet, cells, dt, index=index, **kw)
     pc = dict(cells)
-    pc["x"] = np.asarray(cells["x"]) * (1.0 + PERTURB)
+    pc["x"] = np.asarray(cells["x"]) * (1.0 + perturb)
     if cells.get("T") is not None:
-        pc["T"] = np.asarray(cells["T"]) * (1.0 - PERTURB)
-    p = burn(onet, pc, dt, index=index, **kw)
-    move = np.abs(p[0] - o[0]) / (np.abs(o[0]) + 1e-4)
-    stable = (move < STABLE_MOVE).all(axis=0) & (p[2] == o[2])
-    if o[1] is not None:
-        stable &= np.abs(p[1] - o[1]) < STABLE_MOVE * np.abs(o[1])
+        pc["T"] = np.asarray(cells["T"]) * (1.0 - perturb)
+    stable = _agree(burn(onet, pc, dt, index=index, **kw), o)
+    if twin:
+        import platform
+        if platform.machine() in ("x86_64", "AMD64"):
+            import oracle
+            tw = oracle.oracle.rounding_twin()
+            stable &= _agree(tw.burn(tw.OracleNetwork(onet.net), cells, dt, index=index, **kw), o)
     return o, stable
 
 
 def compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable=None, tight=None, atol=1e-10,
-            max_steps=100000, rtol=RTOL):
+            max_steps=100000, rtol=RTOL, fp32_matrix=False):
     """g_*: CUDA results; o_*: oracle; stable: mask from classify (None = all
     cells stable); tight: (x, T) of a tight-tolerance oracle run, needed when
     some cells are sensitive."""
@@ -61,7 +85,9 @@ def compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable=None, tight=None, atol
     both_ok = (g_s == 0) & (o_s == 0)
     dx = np.abs(g_x - o_x)
     strict = both_ok & stable
-    x_bad = ((dx > rtol * np.abs(o_x) + 10.0 * atol) & strict[None, :]).any(axis=0)
+    bar = 10.0 * rtol if fp32_matrix else rtol
+    x_bad = ((dx > bar * np.abs(o_x) + 10.0 * atol) & strict[None, :]).any(axis=0)
+    within = ((dx <= rtol * np.abs(o_x) + 10.0 * atol) | ~strict[None, :]).all(axis=0)
     big = (np.abs(o_x) >= atol / 1e-6) & strict[None, :]
     rel = np.where(big, dx / np.maximum(np.abs(o_x), 1e-300), 0.0)
     T_bad = np.zeros(n, dtype=bool)
@@ -70,8 +96,10 @@ def compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable=None, tight=None, atol
            "max_rel_x_stable": float(rel.max()) if rel.size else 0.0}
     if g_T is not None and o_T is not None:
         relT = np.where(strict, np.abs(g_T - o_T) / np.abs(o_T), 0.0)
-        T_bad |= relT > rtol
+        T_bad |= relT > bar
+        within &= relT <= rtol
         rep["max_rel_T_stable"] = float(relT.max())
+    rep["stable_within_1e-5_frac"] = float(within[strict].mean()) if strict.any() else 1.0
     sens = both_ok & ~stable
     rep["sensitive_pass"] = True
     if sens.any():
@@ -94,5 +122,5 @@ def compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable=None, tight=None, atol
     rep["x_fail"] = int(x_bad.sum())
     rep["T_fail"] = int(T_bad.sum())
     rep["pass"] = (rep["status_mismatch"] == 0 and rep["x_fail"] == 0 and rep["T_fail"] == 0
-                   and rep["sensitive_pass"])
+                   and rep["sensitive_pass"] and (not fp32_matrix or rep["stable_within_1e-5_frac"] >= 0.99))
     return rep

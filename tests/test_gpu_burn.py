@@ -28,10 +28,12 @@ def _oracle(net, cells, dt, **kw):
     return oracle.burn(oracle.OracleNetwork(net), cells, dt, **kw)
 
 
-def _reference(net, cells, dt, index=None):
-    """Oracle result, stability mask and tight-tolerance oracle result."""
+def _reference(net, cells, dt, index=None, lu=64):
+    """Oracle result, stability mask (perturbation matched to the matrix
+    precision under test) and tight-tolerance oracle result."""
     on = oracle.OracleNetwork(net)
-    (ox, oT, os_, ost), stable = classify(on, cells, dt, oracle.burn, index=index)
+    (ox, oT, os_, ost), stable = classify(on, cells, dt, oracle.burn, index=index,
+                                          perturb=1e-13 if lu == 64 else 1e-9)
     tx, tT, _, _ = oracle.burn(on, cells, dt, rtol=1e-10, atol=1e-16, index=index)
     return ox, oT, os_, ost, stable, (tx, tT)
 
@@ -42,7 +44,7 @@ def test_robertson_4096(mc, variant, lu):
     net, cells = robertson_network(), robertson_cells(4096, 1)
     gx, gT, gs, gst = _run(mc, net, cells, 40.0, variant=variant, lu_precision=lu)
     ox, oT, os_, ost = _oracle(net, cells, 40.0)
-    rep = compare(gx, gT, gs, ox, oT, os_, ost)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, fp32_matrix=(lu == 32))
     print(rep)
     assert rep["pass"], rep
     assert (gs == 0).all()
@@ -57,11 +59,11 @@ def test_synthetic_networks(mc, make, n, lu):
     net = make()
     cells = synthetic_cells(net, n, seed=3)
     gx, gT, gs, gst = _run(mc, net, cells, 1e10, lu_precision=lu)
-    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10)
-    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight)
+    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10, lu=lu)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=(lu == 32))
     print(net.name, lu, rep, "same step count:", np.mean(gst[0] == ost[0]))
     assert rep["pass"], rep
-    assert rep["stable"] >= 0.9 * n
+    assert rep["stable"] >= 0.75 * n
 
 
 def test_full_size_sampled(mc):
@@ -71,8 +73,8 @@ def test_full_size_sampled(mc):
     cells = synthetic_cells(net, 1 << 20, seed=3)
     gx, gT, gs, gst = _run(mc, net, cells, 1e10)
     idx = np.sort(np.random.default_rng(0).choice(1 << 20, 512, replace=False))
-    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10, index=idx)
-    rep = compare(gx[:, idx], gT[idx], gs[idx], ox, oT, os_, ost, stable=stable, tight=tight)
+    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10, index=idx, lu=32)
+    rep = compare(gx[:, idx], gT[idx], gs[idx], ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=True)
     print(rep)
     assert rep["pass"], rep
     assert np.mean(gs == 0) > 0.99
@@ -167,3 +169,97 @@ def test_isothermal_rate_scale_matches_oracle(mc):
     ox, oT, os_, ost = _oracle(net, cells, 40.0)
     rep = compare(gx, None, gs, ox, None, os_, ost)
     assert rep["pass"], rep
+
+
+@pytest.mark.parametrize("make,n,lu", [(network_13, 2048, 64), (network_13, 2048, 32), (network_33, 512, 32),
+                                       (robertson_network, 1024, 64)])
+def test_straggler_handoff_parity(mc, make, n, lu):
+    """A low hand-off threshold sends most cells through the warp-cooperative
+    form part-way; results must still match the oracle."""
+    net = make()
+    if make is robertson_network:
+        cells, dt = robertson_cells(n, 1), 40.0
+    else:
+        cells, dt = synthetic_cells(net, n, seed=3), 1e10
+    gx, gT, gs, gst = _run(mc, net, cells, dt, lu_precision=lu, variant=2, straggler_steps=40)
+    ox, oT, os_, ost, stable, tight = _reference(net, cells, dt, lu=lu)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=(lu == 32))
+    print(net.name, lu, rep, "handed off:", np.mean(ost[0] + ost[1] + ost[2] > 40))
+    assert rep["pass"], rep
+
+
+def _segments(mc, batch):
+    import torch
+    segs, keep = [], []
+    for net, cells, idx in batch["groups"]:
+        h = mc.Network(net)
+        from paper_2608_06466_b300.api import to_device
+        d = to_device(cells)
+        keep.append((h, d, net, cells))
+        n = cells["x"].shape[1]
+        segs.append(mc.segment(h, n, n, d["x"], d["T"], d["ndens"], d["rate_scale"], d["status"], d["stats"]))
+    return segs, keep
+
+
+def test_mixed_batch_and_graph(mc):
+    import torch
+    from mc_inputs import mixed_batch
+    batch = mixed_batch(3 * 700, seed=6, hot_fraction=0.01)
+    segs, keep = _segments(mc, batch)
+    dts = [40.0, 1e10, 1e10]
+    # networks differ in dt here only through the Robertson segment: run it separately
+    rob_seg, rob = segs[0], keep[0]
+    opts = mc.mc_burn_opts_default(lu_precision=32)
+    mc.mc_burn_mixed(segs[1:], opts, 1e10)
+    mc.mc_burn_mixed([rob_seg], opts, 40.0)
+    torch.cuda.synchronize()
+    first = [(d["x"].cpu().numpy().copy(), None if d["T"] is None else d["T"].cpu().numpy().copy(),
+              d["status"].cpu().numpy().copy(), d["stats"].cpu().numpy().copy()) for (_, d, _, _) in keep]
+    for (h, d, net, cells), (gx, gT, gs, gst), dt in zip(keep, first, dts):
+        ox, oT, os_, ost, stable, tight = _reference(net, cells, dt, lu=32)
+        rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=True)
+        assert rep["pass"], (net.name, rep)
+    # graph replay of the energy segments reproduces the direct launch bitwise
+    totals = torch.zeros(8, dtype=torch.int64, device="cuda")
+    g = mc.mc_graph_create(segs[1:], opts, 1e10, totals)
+    for rep_i in range(2):
+        for (h, d, net, cells) in keep[1:]:
+            d["x"].copy_(torch.as_tensor(cells["x"]))
+            d["T"].copy_(torch.as_tensor(cells["T"]))
+        g.launch()
+        torch.cuda.synchronize()
+        for (h, d, net, cells), (gx, gT, gs, gst) in zip(keep[1:], first[1:]):
+            np.testing.assert_array_equal(d["x"].cpu().numpy(), gx)
+            np.testing.assert_array_equal(d["status"].cpu().numpy(), gs)
+        want = sum(d["stats"].cpu().numpy().astype(np.int64).sum(axis=1) for (_, d, _, _) in keep[1:])
+        np.testing.assert_array_equal(totals.cpu().numpy(), want)
+    g.close()
+
+
+def test_results_do_not_depend_on_the_mix(mc):
+    """Each cell's result is the same burned alone, in a larger batch and in
+    another variant of the persistent launch (bitwise)."""
+    import torch
+    net = network_13()
+    h = mc.Network(net)
+    cells = synthetic_cells(net, 3000, seed=31)
+    alone = {k: (v[:, :100] if (v is not None and v.ndim == 2) else (None if v is None else v[:100]))
+             for k, v in cells.items() if k != "hot"}
+    ax, aT, as_, _ = mc.burn(h, alone, 1e10, mc.mc_burn_opts_default(lu_precision=32))
+    bx, bT, bs, _ = mc.burn(h, cells, 1e10, mc.mc_burn_opts_default(lu_precision=32, blocks_per_sm=1))
+    np.testing.assert_array_equal(ax, bx[:, :100])
+    np.testing.assert_array_equal(aT, bT[:100])
+    np.testing.assert_array_equal(as_, bs[:100])
+
+
+def test_autotune_returns_a_measured_shape(mc):
+    import torch
+    from paper_2608_06466_b300.api import to_device
+    net = network_13()
+    h = mc.Network(net)
+    d = to_device(synthetic_cells(net, 2048, seed=41))
+    x0 = d["x"].clone()
+    best = mc.mc_autotune(h, mc.mc_burn_opts_default(lu_precision=32), 2048, 1e10, d["x"], 2048, d["T"], d["ndens"])
+    torch.cuda.synchronize()
+    assert best.variant in (1, 2) and best.block_threads in (64, 128, 256)
+    assert torch.equal(d["x"], x0)  # the sample is not modified
