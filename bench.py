@@ -110,6 +110,61 @@ def cpu_baseline(net, n_sample, seed):
             "ok_fraction": float(np.mean(status == 0))}
 
 
+def serving_measurement(mc, n_sat=6, n_load=8, seed=7):
+    """Serving loop on AMR-box requests (edge L log-uniform in [16, 128], cells
+    = L^3, 50/50 net13 / net33, FP32-matrix path, 150 GB budget): closed-loop
+    saturation, then Poisson arrivals at 0.5x and 0.9x of it. Bounded request
+    counts keep the run within minutes."""
+    import time as _t
+    from mc_inputs import box_request_stream, network_13, network_33, synthetic_cells
+    nets = {"net13": network_13(), "net33": network_33()}
+    handles = {k: mc.Network(v) for k, v in nets.items()}
+    opts = mc.mc_burn_opts_default(lu_precision=32)
+
+    def make(r):
+        net = nets[r["net"]]
+        c = synthetic_cells(net, r["n_cells"], seed=r["cell_seed"])
+        return (r["net"], r["n_cells"], np.ascontiguousarray(c["x"]), c["T"].copy(), c["ndens"].copy(),
+                np.zeros(r["n_cells"], dtype=np.int32))
+
+    def run(stream_reqs, arrivals):
+        srv = mc.Server(0, 150 << 30, opts)
+        bufs = [make(r) for r in stream_reqs]
+        ids = []
+        t0 = _t.perf_counter()
+        for (name, n, x, T, nd, st), ta in zip(bufs, arrivals):
+            wait = ta - (_t.perf_counter() - t0)
+            if wait > 0:
+                _t.sleep(wait)
+            ids.append(srv.submit(handles[name], n, DT, x, n, T, nd, st))
+        srv.drain(3600)
+        span = _t.perf_counter() - t0
+        infos = [srv.poll(i)[1] for i in ids]
+        srv.close()
+        lat = np.array([i.t_done - i.t_submit for i in infos])
+        cells = sum(b[1] for b in bufs)
+        return lat, cells, span, sum(i.n_failed for i in infos)
+
+    sat_reqs = box_request_stream(n_sat, 1.0, seed=seed)
+    lat, cells, span, _ = run(sat_reqs, [0.0] * n_sat)
+    lam_cells = cells / span
+    sizes = np.array([r["n_cells"] for r in box_request_stream(4096, 1.0, seed=seed + 1)])
+    mean_cells = float(sizes.mean())
+    out = {"lambda_sat_cells_per_s": lam_cells, "mean_cells_per_request": mean_cells,
+           "saturation_requests": n_sat, "loads": [],
+           "note": f"{n_load} Poisson requests per load level (bounded so the run ends in minutes)"}
+    for load in (0.5, 0.9):
+        rate = load * lam_cells / mean_cells
+        reqs = box_request_stream(n_load, rate, seed=seed + int(load * 100))
+        arrivals = [r["t_arrive"] for r in reqs]
+        lat, cells, span, failed = run(reqs, arrivals)
+        out["loads"].append({"load": load, "requests": n_load, "rate_req_per_s": rate,
+                             "p50_latency_s": float(np.percentile(lat, 50)),
+                             "p99_latency_s": float(np.percentile(lat, 99)),
+                             "cells_per_s": cells / span, "failed_cells": int(failed)})
+    return out
+
+
 def run_reference(args, rank, world):
     from mc_inputs import network_13
     net = network_13()
@@ -144,6 +199,7 @@ def main():
     ap.add_argument("--cells", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -275,6 +331,10 @@ def main():
                   "max_rel_x_stable": rep["max_rel_x_stable"], "status_mismatch": rep["status_mismatch"],
                   "stable_within_1e-5_frac": rep["stable_within_1e-5_frac"]}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_measurement(mc)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(net, int(os.environ.get("MC_CPU_SAMPLE", "32768")), CELL_SEED)
@@ -302,6 +362,7 @@ def main():
             "fp64_plain": plain,
             "status_ok_fraction": float(np.mean(status == 0)),
             "parity_sample": parity,
+            "serving": serving,
             "per_step_ms": per32,
         }
         print(json.dumps(line), flush=True)

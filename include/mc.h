@@ -208,11 +208,16 @@ mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts, int64_t n
                       mc_burn_opts *best);
 
 /* ---------------------------------------------------------------- serving */
-/* A server keeps burn requests' state in a device pool, admits requests in
- * arrival order while the pool's bytes stay within hbm_budget_bytes, burns
- * admitted work in bounded persistent epochs on its own stream (requests that
- * arrive while others run join the next epoch, so their work overlaps on the
- * device) and copies results back to the caller's buffers. */
+/* A server (paper: state resident in GPU memory, Software design section,
+ * paragraph 3) admits burn requests in arrival order while the bytes of
+ * admitted request state stay within hbm_budget_bytes (a request counts
+ * (n_species + 2) doubles and one int per cell), copies each admitted
+ * request's state into pooled device memory, burns it with the persistent
+ * kernel on one of the server's 8 streams and copies the results back to the
+ * caller's buffers. Requests that arrive while others are on the GPU start as
+ * soon as memory and a stream are free, so their work overlaps on the device
+ * (continuous batching); a host thread does admission and completion, and no
+ * device code waits on the host. */
 typedef struct {
     int32_t state;          /* MC_PENDING or MC_OK */
     int32_t n_failed;       /* cells with status != MC_CELL_OK */

@@ -37,6 +37,10 @@ mc_status cuda_error(cudaError_t e, const char *what);
 void count_launch(int64_t k);
 DNet dnet_of(const mc_network *net);
 mc_status check_opts(const mc_burn_opts *in, mc_burn_opts *out);
+// Scratch of the stream most recently named by scratch_stream() on this thread.
+void scratch_stream(cudaStream_t st);
+void *scratch_detach(int dev, cudaStream_t st);
+void scratch_free(void *h);
 mc_status scratch_get(int dev, int64_t retry_cells, unsigned long long **next, uint32_t **rcount,
                       int32_t **retry);
 mc_status burn_device(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st);

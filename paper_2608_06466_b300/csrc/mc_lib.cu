@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -169,24 +170,66 @@ DNet mc::dnet_of(const mc_network *net) {
 }
 
 // ---------------------------------------------------------------- device scratch
-// Library-owned scratch per device: the persistent queue counter and the
-// FP32 pass's retry list (grown on demand, never shrunk).
+// Library-owned scratch, one set per (device, stream) so burns issued on
+// different streams never share queue counters or lists: the persistent queue
+// counters, the FP32 pass's retry lists and the straggler records (each grown
+// on demand, never shrunk).
 namespace {
 struct DevScratch {
   unsigned long long *next = nullptr;   // [MAX_QUEUES] queue counters
   uint32_t *retry_count = nullptr;      // [MAX_QUEUES] retry-list lengths
   int32_t *retry = nullptr;             // retry lists (cells)
   int64_t retry_cap = 0;
+  void *rec = nullptr;                  // straggler records
+  uint32_t *rec_count = nullptr;
+  size_t rec_bytes = 0;
 };
 std::mutex g_scratch_mu;
-DevScratch g_scratch[64];
+std::map<std::pair<int, uintptr_t>, DevScratch> g_scratch;
+
+thread_local cudaStream_t g_cur_stream = nullptr;
+
+DevScratch &scratch_of(int dev) {
+  return g_scratch[std::make_pair(dev, (uintptr_t)g_cur_stream)];
+}
+
+// the old buffer may still be read by work queued on this stream
+cudaError_t retire(void *p) {
+  if (!p) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(g_cur_stream);
+  cudaFree(p);
+  return e;
+}
 }  // namespace
+
+void mc::scratch_stream(cudaStream_t st) { g_cur_stream = st; }
+
+// Hand the scratch set of (dev, st) to the caller (a graph that keeps using it
+// after its capture stream is gone); free it with scratch_free.
+void *mc::scratch_detach(int dev, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  auto it = g_scratch.find(std::make_pair(dev, (uintptr_t)st));
+  if (it == g_scratch.end()) return nullptr;
+  DevScratch *d = new DevScratch(it->second);
+  g_scratch.erase(it);
+  return d;
+}
+
+void mc::scratch_free(void *h) {
+  DevScratch *d = (DevScratch *)h;
+  if (!d) return;
+  cudaFree(d->next);
+  cudaFree(d->retry);
+  cudaFree(d->rec);
+  cudaFree(d->rec_count);
+  delete d;
+}
 
 mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **next, uint32_t **rcount,
                           int32_t **retry) {
-  if (dev < 0 || dev >= 64) return set_error(MC_E_INVALID, "device %d out of range", dev);
+  if (dev < 0) return set_error(MC_E_INVALID, "device %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  DevScratch &s = g_scratch[dev];
+  DevScratch &s = scratch_of(dev);
   cudaError_t e;
   if (!s.next) {
     e = cudaMalloc(&s.next, (sizeof(unsigned long long) + sizeof(uint32_t)) * MAX_QUEUES);
@@ -194,14 +237,10 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
     s.retry_count = (uint32_t *)(s.next + MAX_QUEUES);
   }
   if (retry_cells > s.retry_cap) {
-    // the old list may still be read by work queued on another stream
-    if (s.retry) {
-      e = cudaDeviceSynchronize();
-      if (e != cudaSuccess) return cuda_error(e, "scratch grow sync");
-      cudaFree(s.retry);
-      s.retry = nullptr;
-      s.retry_cap = 0;
-    }
+    e = retire(s.retry);
+    s.retry = nullptr;
+    s.retry_cap = 0;
+    if (e != cudaSuccess) return cuda_error(e, "scratch grow sync");
     e = cudaMalloc(&s.retry, sizeof(int32_t) * retry_cells);
     if (e != cudaSuccess) return cuda_error(e, "retry list allocation");
     s.retry_cap = retry_cells;
@@ -212,40 +251,27 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
   return MC_OK;
 }
 
-namespace {
-struct StragScratch {
-  void *rec = nullptr;
-  uint32_t *count = nullptr;
-  size_t bytes = 0;
-};
-StragScratch g_strag[64];
-}  // namespace
-
 mc_status mc::straggler_scratch(size_t bytes, void **rec, uint32_t **count) {
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return set_error(MC_E_INVALID, "device %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  StragScratch &s = g_strag[dev];
+  DevScratch &s = scratch_of(dev);
   cudaError_t e;
-  if (!s.count) {
-    e = cudaMalloc(&s.count, 256);
+  if (!s.rec_count) {
+    e = cudaMalloc(&s.rec_count, 256);
     if (e != cudaSuccess) return cuda_error(e, "straggler counter allocation");
   }
-  if (bytes > s.bytes) {
-    if (s.rec) {
-      e = cudaDeviceSynchronize();
-      if (e != cudaSuccess) return cuda_error(e, "straggler grow sync");
-      cudaFree(s.rec);
-      s.rec = nullptr;
-      s.bytes = 0;
-    }
+  if (bytes > s.rec_bytes) {
+    e = retire(s.rec);
+    s.rec = nullptr;
+    s.rec_bytes = 0;
+    if (e != cudaSuccess) return cuda_error(e, "straggler grow sync");
     e = cudaMalloc(&s.rec, bytes);
     if (e != cudaSuccess) return cuda_error(e, "straggler record allocation");
-    s.bytes = bytes;
+    s.rec_bytes = bytes;
   }
   *rec = s.rec;
-  *count = s.count;
+  *count = s.rec_count;
   return MC_OK;
 }
 
@@ -302,6 +328,7 @@ mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const C
                           cudaStream_t st) {
   int dev = 0;
   cudaGetDevice(&dev);
+  scratch_stream(st);
   Tuned tu = autotune_pick(net, ob);
   Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps};
   const DNet d = dnet_of(net);

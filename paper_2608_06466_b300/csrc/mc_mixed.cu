@@ -56,6 +56,7 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
   unsigned long long *next;
   uint32_t *rcount;
   int32_t *retry;
+  scratch_stream(st);
   mc_status rs = scratch_get(dev, ob.lu_precision == 32 ? total : 0, &next, &rcount, &retry);
   if (rs != MC_OK) return rs;
   MixedArgs m{};
@@ -141,6 +142,7 @@ struct mc_graph {
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;
   int device = 0;
+  void *scratch = nullptr;   // scratch set the captured kernels use
 };
 
 extern "C" mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, const mc_burn_opts *opts,
@@ -162,11 +164,16 @@ extern "C" mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, con
   unsigned long long *next;
   uint32_t *rcount;
   int32_t *retry;
-  s = scratch_get(dev, o.lu_precision == 32 ? total : 0, &next, &rcount, &retry);
-  if (s != MC_OK) return s;
   cudaStream_t cs;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_error(e, "capture stream");
+  // the graph keeps the scratch set of its capture stream (allocated here, before capture)
+  scratch_stream(cs);
+  s = scratch_get(dev, o.lu_precision == 32 ? total : 0, &next, &rcount, &retry);
+  if (s != MC_OK) {
+    cudaStreamDestroy(cs);
+    return s;
+  }
   mc_graph *g = new mc_graph();
   g->device = dev;
   const int64_t before = mc_launch_count(0);
@@ -197,12 +204,14 @@ extern "C" mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, con
     e = cudaGraphInstantiate(&g->exec, g->graph, 0);
     if (e != cudaSuccess) s = cuda_error(e, "graph instantiate");
   }
+  g->scratch = scratch_detach(dev, cs);
   cudaStreamDestroy(cs);
   g->kernels = mc_launch_count(0) - before;
   mc_launch_count(1);
   count_launch(before);  // captured launches did not run
   if (s != MC_OK) {
     if (g->graph) cudaGraphDestroy(g->graph);
+    scratch_free(g->scratch);
     delete g;
     return s;
   }
@@ -222,6 +231,8 @@ extern "C" mc_status mc_graph_destroy(mc_graph *g) {
   if (!g) return MC_OK;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  cudaDeviceSynchronize();  // replays may still be using the scratch set
+  scratch_free(g->scratch);
   delete g;
   return MC_OK;
 }
