@@ -165,6 +165,28 @@ mc_status mc_network_rhs(const mc_network *net, int64_t n, const double *y, int6
                          const double *ndens, const double *rate_scale, double *f, double *jac, int32_t *ok,
                          void *stream);
 
+/* Burn without allocating any memory (no counterpart in the paper; a library
+ * service). For callers that cannot let a library call cudaMalloc -- programs
+ * that give all device memory to their own arena up front and must not see
+ * allocations appear later, or latency-critical loops that cannot afford
+ * cudaMalloc's implicit synchronisation. Same arguments and results as
+ * mc_burn_batch with the persistent variant, except:
+ *   - cell arrays must be device memory, and n_cells <= MC_NOALLOC_MAX_CELLS
+ *     (larger batches are rejected with MC_E_INVALID before any work);
+ *   - its scratch is a fixed file-scope device array of 256 bytes plus 4 bytes
+ *     per cell of that maximum (about 4 MB), held by every GPU that loads the
+ *     library until the process exits; no straggler hand-off is done;
+ *   - the first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture;
+ *   - every call shares the one array: it clears what must start at zero on
+ *     the stream, but calls whose work overlaps on the GPU (different streams,
+ *     or another thread) race and corrupt each other's results. */
+#define MC_NOALLOC_MAX_CELLS (1 << 20)
+mc_status mc_burn_batch_noalloc(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells, double dt,
+                                double *x, int64_t ld, double *T, const double *ndens,
+                                const double *rate_scale, int32_t *status, int32_t *stats, void *stream);
+
 /* One segment of a mixed batch: cells that share a network, laid out as in
  * mc_burn_batch (device pointers). */
 typedef struct {

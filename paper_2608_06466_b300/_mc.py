@@ -72,6 +72,9 @@ _sig("mc_network_n_ode", C.c_int32, [C.c_void_p])
 _sig("mc_burn_batch", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p,
                                   C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p])
+_sig("mc_burn_batch_noalloc", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p,
+                                          C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p])
 _sig("mc_burn_mixed", C.c_int32, [C.POINTER(mc_segment), C.c_int32, C.POINTER(mc_burn_opts), C.c_double,
                                   C.c_void_p])
 _sig("mc_graph_create", C.c_int32, [C.POINTER(mc_segment), C.c_int32, C.POINTER(mc_burn_opts), C.c_double,
@@ -188,6 +191,19 @@ def mc_burn_batch(net: Network, opts: mc_burn_opts | None, n_cells: int, dt: flo
     return check(lib.mc_burn_batch(net.handle, C.byref(o), int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T),
                                    _ptr(ndens), _ptr(rate_scale), _ptr(status), _ptr(stats),
                                    _stream_ptr(stream)), "mc_burn_batch")
+
+
+MC_NOALLOC_MAX_CELLS = 1 << 20
+
+
+def mc_burn_batch_noalloc(net: Network, opts: mc_burn_opts | None, n_cells: int, dt: float, x, ld: int, T, ndens,
+                          rate_scale, status, stats, stream=None) -> int:
+    """The allocation-free burn: device arrays only, n_cells <= MC_NOALLOC_MAX_CELLS,
+    scratch in a fixed device array shared by all calls (overlapping calls race)."""
+    o = opts if opts is not None else mc_burn_opts_default()
+    return check(lib.mc_burn_batch_noalloc(net.handle, C.byref(o), int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T),
+                                           _ptr(ndens), _ptr(rate_scale), _ptr(status), _ptr(stats),
+                                           _stream_ptr(stream)), "mc_burn_batch_noalloc")
 
 
 def segment(net: Network, n_cells, ld, x, T, ndens, rate_scale, status, stats) -> mc_segment:

@@ -44,6 +44,11 @@ void scratch_free(void *h);
 mc_status scratch_get(int dev, int64_t retry_cells, unsigned long long **next, uint32_t **rcount,
                       int32_t **retry);
 mc_status burn_device(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st);
+mc_status burn_device_scratch(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st,
+                              unsigned long long *next, uint32_t *rcount, int32_t *retry, bool allow_strag);
+mc_status check_batch(const mc_network *net, int64_t n_cells, double dt, double *x, int64_t ld, double *T,
+                      const double *ndens, const double *rate_scale, int32_t *status, int32_t *stats,
+                      bool *on_dev);
 
 // launch shape chosen for a network and options
 struct Tuned {

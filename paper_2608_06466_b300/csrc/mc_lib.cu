@@ -322,21 +322,17 @@ mc_status mc::check_opts(const mc_burn_opts *opts, mc_burn_opts *o) {
   return MC_OK;
 }
 
-// Burn one segment on the device (device pointers). Runs the FP32 pass and,
-// when it leaves Newton failures behind, the FP64 retry pass over them.
-mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const CellArgs &a0,
-                          cudaStream_t st) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  scratch_stream(st);
+// Burn one segment on the device (device pointers) with the given scratch:
+// queue counters next[0..1], the FP32 pass's retry count and list (n_cells
+// entries). Runs the FP32 pass and, when it leaves Newton failures behind, the
+// FP64 retry pass over them. Straggler hand-off only when allow_strag.
+mc_status mc::burn_device_scratch(const mc_network *net, const mc_burn_opts &ob, const CellArgs &a0,
+                                  cudaStream_t st, unsigned long long *next, uint32_t *rcount, int32_t *retry,
+                                  bool allow_strag) {
   Tuned tu = autotune_pick(net, ob);
+  if (!allow_strag) tu.strag_steps = 0;
   Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps};
   const DNet d = dnet_of(net);
-  unsigned long long *next;
-  uint32_t *rcount;
-  int32_t *retry;
-  mc_status s = scratch_get(dev, ob.lu_precision == 32 ? a0.n_cells : 0, &next, &rcount, &retry);
-  if (s != MC_OK) return s;
   if (ob.lu_precision == 64)
     return dispatch<double>(net, d, o, a0, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);
   CellArgs a = a0;
@@ -344,7 +340,7 @@ mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const C
   a.retry_count = rcount;
   cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_error(e, "retry counter reset");
-  s = dispatch<float>(net, d, o, a, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);
+  mc_status s = dispatch<float>(net, d, o, a, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);
   if (s != MC_OK) return s;
   // FP64 pass over the list; its length is read on the device
   CellArgs b = a0;
@@ -354,29 +350,58 @@ mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const C
   return dispatch<double>(net, d, o, b, MC_VARIANT_PERSISTENT, tu.threads, tu.blocks_per_sm, 0, next, st);
 }
 
+// Burn with the library scratch set of stream st.
+mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const CellArgs &a0,
+                          cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  scratch_stream(st);
+  unsigned long long *next;
+  uint32_t *rcount;
+  int32_t *retry;
+  mc_status s = scratch_get(dev, ob.lu_precision == 32 ? a0.n_cells : 0, &next, &rcount, &retry);
+  if (s != MC_OK) return s;
+  return burn_device_scratch(net, ob, a0, st, next, rcount, retry, true);
+}
+
+// Shared argument checks of the batch entry points. *on_dev tells whether the
+// cell arrays are device (true) or host memory.
+mc_status mc::check_batch(const mc_network *net, int64_t n_cells, double dt, double *x, int64_t ld, double *T,
+                          const double *ndens, const double *rate_scale, int32_t *status, int32_t *stats,
+                          bool *on_dev) {
+  if (!net) return set_error(MC_E_INVALID, "null network");
+  if (n_cells < 0 || ld < n_cells || n_cells > (int64_t)INT32_MAX)
+    return set_error(MC_E_INVALID, "need 0 <= n_cells <= ld and n_cells < 2^31");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(MC_E_INVALID, "dt must be positive");
+  if (n_cells == 0) {
+    *on_dev = true;
+    return MC_OK;
+  }
+  if (!x || !status) return set_error(MC_E_INVALID, "x and status are required");
+  if (net->energy && !T) return set_error(MC_E_INVALID, "energy networks need T");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != net->device) return set_error(MC_E_INVALID, "network lives on device %d, current is %d", net->device, dev);
+  const bool d = is_device_ptr(x);
+  if (d != is_device_ptr(status) || (T && d != is_device_ptr(T)) || (ndens && d != is_device_ptr(ndens)) ||
+      (rate_scale && d != is_device_ptr(rate_scale)) || (stats && d != is_device_ptr(stats)))
+    return set_error(MC_E_INVALID, "mix of host and device arrays");
+  *on_dev = d;
+  return MC_OK;
+}
+
 extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
                                    double dt, double *x, int64_t ld, double *T, const double *ndens,
                                    const double *rate_scale, int32_t *status, int32_t *stats,
                                    void *stream) {
-  if (!net) return set_error(MC_E_INVALID, "mc_burn_batch: null network");
   mc_burn_opts o;
   mc_status s = check_opts(opts, &o);
   if (s != MC_OK) return s;
-  if (n_cells < 0 || ld < n_cells || n_cells > (int64_t)INT32_MAX)
-    return set_error(MC_E_INVALID, "mc_burn_batch: need 0 <= n_cells <= ld and n_cells < 2^31");
-  if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(MC_E_INVALID, "mc_burn_batch: dt must be positive");
+  bool on_dev = true;
+  s = check_batch(net, n_cells, dt, x, ld, T, ndens, rate_scale, status, stats, &on_dev);
+  if (s != MC_OK) return s;
   if (n_cells == 0) return MC_OK;
-  if (!x || !status) return set_error(MC_E_INVALID, "mc_burn_batch: x and status are required");
-  if (net->energy && !T) return set_error(MC_E_INVALID, "mc_burn_batch: energy networks need T");
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev != net->device) return set_error(MC_E_INVALID, "network lives on device %d, current is %d", net->device, dev);
   cudaStream_t st = (cudaStream_t)stream;
-  const bool on_dev = is_device_ptr(x);
-  if (on_dev != is_device_ptr(status) || (T && on_dev != is_device_ptr(T)) ||
-      (ndens && on_dev != is_device_ptr(ndens)) || (rate_scale && on_dev != is_device_ptr(rate_scale)) ||
-      (stats && on_dev != is_device_ptr(stats)))
-    return set_error(MC_E_INVALID, "mc_burn_batch: mix of host and device arrays");
   CellArgs a{};
   a.n_cells = n_cells;
   a.ld = ld;
