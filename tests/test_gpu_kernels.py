@@ -27,26 +27,38 @@ def _ulp_diff(a, b):
 
 
 def test_rate_exponential_within_few_ulp_of_cuda_exp(mc):
+    """With b = C = 0 a rate coefficient is exactly exp(ln A) of the stored
+    ln A, so the table-driven exponential can be compared with CUDA's exp on
+    bit-identical arguments, over the whole double range (normal and
+    subnormal results)."""
     import torch
-    net = network_33()
-    h = mc.Network(net)
-    n = 1 << 16
+    from mc_inputs.networks import Network
+    R = 512
     rng = np.random.default_rng(1)
-    T = torch.as_tensor(np.exp(rng.uniform(np.log(5.0), np.log(2e5), n)), device="cuda")
-    kf = torch.empty((net.n_reactions, n), dtype=torch.float64, device="cuda")
+    v = np.concatenate([rng.uniform(-744.0, 709.0, R - 64), rng.uniform(-745.0, -700.0, 32),
+                        rng.uniform(-1.0, 1.0, 32)])
+    A = np.exp(v)
+    A[A == 0] = 5e-324
+    z = np.zeros(R)
+    net = Network(name="exptest", n_species=2, n_elements=1, energy_eq=False,
+                  react=np.tile(np.array([[0, -1]], dtype=np.int32), (R, 1)),
+                  prod=np.tile(np.array([[1, -1]], dtype=np.int32), (R, 1)),
+                  composition=np.ones((2, 1), dtype=np.int32), A_f=A, b_f=z.copy(), C_f=z.copy(),
+                  A_r=z.copy(), b_r=z.copy(), C_r=z.copy(), dE_eV=z.copy())
+    h = mc.Network(net)
+    n = 64
+    T = torch.full((n,), 300.0, dtype=torch.float64, device="cuda")
+    kf = torch.empty((R, n), dtype=torch.float64, device="cuda")
     kr = torch.empty_like(kf)
     mc.mc_network_rates(h, n, T, kf, kr, n)
-    lnT, invT = torch.log(T), 1.0 / T
-    lnAf = torch.as_tensor(np.log(net.A_f), device="cuda")[:, None]
-    ref = torch.exp(lnAf + torch.as_tensor(net.b_f, device="cuda")[:, None] * lnT
-                    - torch.as_tensor(net.C_f, device="cuda")[:, None] * invT)
+    ref = torch.exp(torch.log(torch.as_tensor(A, device="cuda")))[:, None].expand(R, n)
     torch.cuda.synchronize()
     a, b = kf.cpu().numpy(), ref.cpu().numpy()
-    normal = (b > 2.3e-308) & (b < 1e300)
-    d = _ulp_diff(a[normal], b[normal])
-    assert d.max() <= 4, d.max()
-    sub = ~normal & (b >= 0)
-    np.testing.assert_allclose(a[sub], b[sub], rtol=0, atol=1e-320)
+    normal = b > 2.2250738585072014e-308
+    assert _ulp_diff(a[normal], b[normal]).max() <= 2
+    # subnormal results: within one unit of the smallest subnormal spacing
+    assert np.abs(a[~normal] - b[~normal]).max() <= 1e-323
+    assert (kr.cpu().numpy() == 0).all()
 
 
 @pytest.mark.parametrize("make", [robertson_network, network_13, network_33])
