@@ -83,6 +83,7 @@ typedef int32_t mc_status;
 #define MC_VARIANT_AUTO 0       /* autotuner's choice */
 #define MC_VARIANT_PLAIN 1      /* one thread per cell, one launch over the cells */
 #define MC_VARIANT_PERSISTENT 2 /* persistent workers pulling cells from a queue */
+#define MC_VARIANT_WARP 3       /* persistent, one warp per cell (large networks) */
 
 typedef struct mc_network mc_network;
 typedef struct mc_server mc_server;

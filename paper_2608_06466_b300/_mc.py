@@ -26,7 +26,7 @@ ERRORS = {-1: "MC_E_INVALID", -2: "MC_E_NOMEM", -3: "MC_E_CUDA", -4: "MC_E_BUSY"
 CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "conv_fail", 4: "bad_input", 5: "nonfinite"}
 STAT_NAMES = ["steps", "err_fails", "conv_fails", "rhs", "jac", "lu", "newton", "order"]
 MC_NSTAT = 8
-MC_VARIANT_AUTO, MC_VARIANT_PLAIN, MC_VARIANT_PERSISTENT = 0, 1, 2
+MC_VARIANT_AUTO, MC_VARIANT_PLAIN, MC_VARIANT_PERSISTENT, MC_VARIANT_WARP = 0, 1, 2, 3
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)

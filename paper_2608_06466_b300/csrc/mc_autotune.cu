@@ -74,7 +74,9 @@ void save_entry(const Key &k, const Tuned &t) {
 }  // namespace
 
 Tuned mc::autotune_pick(const mc_network *net, const mc_burn_opts &o) {
-  Tuned t{MC_VARIANT_PERSISTENT, 128, 2, 2048};
+  // defaults: thread-per-cell with hand-off for small networks, warp-per-cell
+  // above 16 ODEs (the per-cell matrices no longer fit a lane's share of L1)
+  Tuned t{(net && net->n > 16) ? MC_VARIANT_WARP : MC_VARIANT_PERSISTENT, 128, 2, 2048};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();
@@ -116,6 +118,7 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
   for (int thr : {64, 128, 256}) cands.push_back({MC_VARIANT_PLAIN, thr, 0});
   for (int thr : {64, 128, 256})
     for (int bps : {1, 2, 4}) cands.push_back({MC_VARIANT_PERSISTENT, thr, bps});
+  for (int bps : {1, 2, 4}) cands.push_back({MC_VARIANT_WARP, 128, bps});
   float best_ms = 1e30f;
   Cand win = cands[0];
   for (const Cand &c : cands) {

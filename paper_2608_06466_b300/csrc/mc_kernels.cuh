@@ -148,7 +148,7 @@ struct StragArgs {
 // every lane's cell is stored or handed off.
 template <int N, typename LT>
 __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs &a,
-                                  unsigned long long *next, const StragArgs &sa) {
+                                  unsigned long long *next, const StragArgs &sa, double *tsm) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t total = count_of(a);
@@ -174,8 +174,9 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
       }
     }
     if (!__any_sync(FULL, L.phase != PH_IDLE)) break;
-    if (L.phase != PH_IDLE && L.phase != PH_DONE) {
-      const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
+    const bool busy = L.phase != PH_IDLE && L.phase != PH_DONE;
+    if (busy) {
+      const bool ok = tsm ? net_rhs_sm<N>(net, L.cin, L.y, L.f, tsm) : net_rhs<N>(net, L.cin, L.y, L.f);
       advance(L, net, o, ok);
       run_stages(L, net, o);
       if (sa.rec && L.phase == PH_NEWTON && L.m == 0 && L.attempts >= sa.threshold && !L.kept) {
@@ -191,43 +192,15 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
   }
 }
 
+// Shared memory per warp for net_rhs_sm (0 when it does not fit: net_rhs then).
+__host__ __device__ inline size_t thread_rhs_smem(int N, int R) { return sizeof(double) * 32 * (size_t)(N + R); }
+
 template <int N, typename LT>
 __global__ void __launch_bounds__(256) k_burn_persistent(DNet net, Opts o, CellArgs a,
-                                                         unsigned long long *next, StragArgs sa) {
-  persistent_worker<N, LT>(net, o, a, next, sa);
-}
-
-// One segment of a mixed launch: a network, its cells and its compiled bucket.
-struct SegDev {
-  DNet net;
-  CellArgs a;
-  int bucket;
-};
-
-constexpr int MIXED_MAX_SEGS = 8;
-
-struct MixedArgs {
-  SegDev seg[MIXED_MAX_SEGS];
-  int nseg;
-};
-
-// Mixed persistent launch: every warp drains the segment queues starting at a
-// segment chosen by its warp index, so all networks start at once and warps
-// that finish one network move on to the next (one launch for all networks).
-template <typename LT>
-__global__ void __launch_bounds__(256) k_burn_mixed(MixedArgs m, Opts o, unsigned long long *next) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const StragArgs sa{nullptr, nullptr, 0u, 0};
-  for (int s0 = 0; s0 < m.nseg; ++s0) {
-    const int s = (s0 + warp) % m.nseg;
-    const SegDev &g = m.seg[s];
-    switch (g.bucket) {
-      case 3: persistent_worker<3, LT>(g.net, o, g.a, next + s, sa); break;
-      case 13: persistent_worker<13, LT>(g.net, o, g.a, next + s, sa); break;
-      case 33: persistent_worker<33, LT>(g.net, o, g.a, next + s, sa); break;
-      default: persistent_worker<40, LT>(g.net, o, g.a, next + s, sa); break;
-    }
-  }
+                                                         unsigned long long *next, StragArgs sa, int tsm_per_warp) {
+  extern __shared__ __align__(16) unsigned char tsmem[];
+  double *tsm = tsm_per_warp ? (double *)(tsmem + (threadIdx.x >> 5) * (size_t)tsm_per_warp) : nullptr;
+  persistent_worker<N, LT>(net, o, a, next, sa, tsm);
 }
 
 }  // namespace mc

@@ -17,7 +17,23 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
-  if (variant == MC_VARIANT_PLAIN) {
+  if (variant == MC_VARIANT_WARP) {
+    e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_error(e, "queue reset");
+    const int per_warp = (int)wsh_bytes<N, LT>(d.R);
+    const int wthreads = 128;
+    const int smem = per_warp * (wthreads / 32);
+    static thread_local int configured_w = 0;
+    if (configured_w < smem) {
+      e = cudaFuncSetAttribute(k_burn_warp<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return cuda_error(e, "warp kernel smem attribute");
+      configured_w = smem;
+    }
+    int64_t blocks = (int64_t)sms * std::max(1, blocks_per_sm) * 2;
+    const int64_t need = a.n_dev ? blocks : (a.n_cells + 3) / 4;
+    blocks = std::max<int64_t>(1, std::min(blocks, need));
+    k_burn_warp<N, LT><<<(unsigned)blocks, wthreads, smem, st>>>(d, o, a, next, per_warp);
+  } else if (variant == MC_VARIANT_PLAIN) {
     if (a.n_cells <= 0) return MC_OK;
     const int64_t blocks = (a.n_cells + threads - 1) / threads;
     k_burn_plain<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a);
@@ -38,7 +54,21 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
       e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
       if (e != cudaSuccess) return cuda_error(e, "straggler counter reset");
     }
-    k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
+    // per-warp shared slices for the gather form of the right-hand side
+    const size_t tsm = thread_rhs_smem(N, d.R);
+    int tsm_per_warp = 0;
+    if (d.R <= 128 && tsm * (threads / 32) <= 96 * 1024) {
+      tsm_per_warp = (int)tsm;
+      static thread_local int configured_t = 0;
+      const int bytes = tsm_per_warp * (threads / 32);
+      if (configured_t < bytes) {
+        e = cudaFuncSetAttribute(k_burn_persistent<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return cuda_error(e, "persistent kernel smem attribute");
+        configured_t = bytes;
+      }
+    }
+    k_burn_persistent<N, LT><<<(unsigned)blocks, threads, tsm_per_warp * (threads / 32), st>>>(d, o, a, next, sa,
+                                                                                               tsm_per_warp);
     if (sa.rec) {
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_error(e, "burn kernel launch");

@@ -314,7 +314,7 @@ mc_status mc::check_opts(const mc_burn_opts *opts, mc_burn_opts *o) {
   if (o->max_steps < 1) return set_error(MC_E_INVALID, "max_steps must be positive");
   if (o->lu_precision != 64 && o->lu_precision != 32)
     return set_error(MC_E_INVALID, "lu_precision must be 64 or 32");
-  if (o->variant < 0 || o->variant > MC_VARIANT_PERSISTENT) return set_error(MC_E_INVALID, "unknown variant");
+  if (o->variant < 0 || o->variant > MC_VARIANT_WARP) return set_error(MC_E_INVALID, "unknown variant");
   if (o->block_threads < 0 || o->block_threads > 1024 || (o->block_threads % 32) != 0)
     return set_error(MC_E_INVALID, "block_threads must be a multiple of 32 up to 1024");
   if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) return set_error(MC_E_INVALID, "blocks_per_sm must be 0..32");

@@ -13,7 +13,7 @@
 #include <vector>
 
 #include "mc_internal.h"
-#include "mc_kernels.cuh"
+#include "mc_warp.cuh"
 
 using namespace mc;
 
@@ -88,14 +88,51 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
   }
   Tuned tu = autotune_pick(nullptr, ob);
   const Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps};
+  // shared workspace of the warp-per-cell segments (the largest one)
+  size_t per_warp = 16;
+  for (int s = 0; s < nseg; ++s) {
+    const int b = m.seg[s].bucket, R = segs[s].net->R;
+    if (b == 33) per_warp = std::max(per_warp, ob.lu_precision == 64 ? wsh_bytes<33, double>(R) : wsh_bytes<33, float>(R));
+    if (b == 40) per_warp = std::max(per_warp, ob.lu_precision == 64 ? wsh_bytes<40, double>(R) : wsh_bytes<40, float>(R));
+  }
+  // thread-per-cell segments gather their right-hand sides in the same region
+  bool tsm_ok = true;
+  size_t tsm_need = 0;
+  for (int s = 0; s < nseg; ++s) {
+    const int b = m.seg[s].bucket, R = segs[s].net->R;
+    if (b == 3 || b == 13) {
+      if (R > 128) tsm_ok = false;
+      tsm_need = std::max(tsm_need, thread_rhs_smem(b, R));
+    }
+  }
+  if (tsm_ok && std::max(per_warp, tsm_need) * 4 <= 160 * 1024) {
+    per_warp = std::max(per_warp, tsm_need);
+    m.thread_smem = 1;
+  } else {
+    m.thread_smem = 0;
+  }
+  m.smem_per_warp = (int)per_warp;
+  const int mthreads = 128;
+  const int msmem = (int)per_warp * (mthreads / 32);
+  {
+    // both precisions run in one call (FP32 pass, FP64 retry pass)
+    static thread_local int configured = 0;
+    if (configured < msmem) {
+      cudaError_t ea = cudaFuncSetAttribute(k_burn_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
+      if (ea == cudaSuccess)
+        ea = cudaFuncSetAttribute(k_burn_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
+      if (ea != cudaSuccess) return cuda_error(ea, "mixed smem attribute");
+      configured = msmem;
+    }
+  }
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long) * nseg, st);
   if (e == cudaSuccess && ob.lu_precision == 32) e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t) * nseg, st);
   if (e != cudaSuccess) return cuda_error(e, "mixed queue reset");
   const unsigned blocks = (unsigned)std::max(1, sms * tu.blocks_per_sm);
   if (ob.lu_precision == 64) {
-    k_burn_mixed<double><<<blocks, tu.threads, 0, st>>>(m, o, next);
+    k_burn_mixed<double><<<blocks, mthreads, msmem, st>>>(m, o, next);
   } else {
-    k_burn_mixed<float><<<blocks, tu.threads, 0, st>>>(m, o, next);
+    k_burn_mixed<float><<<blocks, mthreads, msmem, st>>>(m, o, next);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "mixed launch");
     count_launch(1);
@@ -112,7 +149,7 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     }
     e = cudaMemsetAsync(next, 0, sizeof(unsigned long long) * nseg, st);
     if (e != cudaSuccess) return cuda_error(e, "mixed queue reset");
-    k_burn_mixed<double><<<blocks, tu.threads, 0, st>>>(r, o, next);
+    k_burn_mixed<double><<<blocks, mthreads, msmem, st>>>(r, o, next);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "mixed launch");

@@ -134,6 +134,66 @@ __device__ __forceinline__ void w_load(WState<N> &W, const Lane<N, LT> &L, const
   __syncwarp();
 }
 
+// Load cell c straight from the cell arrays (warp form of load_cell): same
+// input checks; sets PH_F0, or PH_DONE with CELL_BAD_INPUT (m = -1: outputs are
+// then left untouched).
+template <int N>
+__device__ __forceinline__ void w_load_cell(WState<N> &W, const DNet &net, const CellArgs &a, int64_t c) {
+  constexpr int NS = WState<N>::NS;
+  const int S = net.S, n = net.n, ln = wlane();
+  W.cell = c;
+  W.status = CELL_OK;
+  W.q = 0;
+  for (int k = 0; k < NSTAT; ++k) W.st[k] = 0;
+  bool bad = false;
+  double xs = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int i = ln + 32 * k;
+    const double v = (i < S) ? a.x[i * a.ld + c] : 0.0;
+#pragma unroll
+    for (int j = 0; j < QMAX + 2; ++j) W.z[j][k] = 0.0;
+    W.z[0][k] = v;
+    W.e[k] = 0.0;
+    W.es[k] = 0.0;
+    W.f[k] = 0.0;
+    if (i < S) {
+      xs += v;
+      if (!isfinite(v)) bad = true;
+    }
+  }
+  const double X = wsum(xs);
+  const double nd = a.nd ? a.nd[c] : 1.0;
+  const double T = a.T ? a.T[c] : 1.0;
+  bool good = !__any_sync(WFULL, bad) && nd > 0.0 && isfinite(nd) && T > 0.0 && isfinite(T);
+  W.cin.nd = nd;
+  W.cin.ks = a.ks ? a.ks + c : nullptr;
+  W.cin.ks_ld = a.ld;
+  if (net.energy) {
+    if (!(X > 0.0) || !isfinite(X)) good = false;
+    const double u = X * KB_EV * T / net.gm1;
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      if (ln + 32 * k == S) W.z[0][k] = u;
+    W.cin.lnT = 0.0;
+    W.cin.invT = 0.0;
+  } else {
+    W.cin.lnT = log(T);
+    W.cin.invT = 1.0 / T;
+  }
+  if (!good) {
+    W.status = CELL_BAD_INPUT;
+    W.phase = PH_DONE;
+    W.m = -1;
+    return;
+  }
+  W.m = 0;
+  W.tend = a.dt;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) W.y[k] = (ln + 32 * k < n) ? W.z[0][k] : 0.0;
+  W.phase = PH_F0;
+}
+
 // temperature quantities of the point in sh.yb (energy form) or of the cell
 __device__ __forceinline__ bool w_temperature(const DNet &net, const CellIn &c, const double *yb, double &T,
                                               double &X, double &lnT, double &invT) {
@@ -707,10 +767,65 @@ __device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, co
   return 0;
 }
 
-// Consume f(y) (only the phases a handed-off cell can be in).
+// Consume f(y) according to the cell's phase.
 template <int N, typename LT>
 __device__ __forceinline__ void w_advance(WState<N> &W, const WSh<LT> &sh, const DNet &net, const Opts &o, bool ok) {
   constexpr int NS = WState<N>::NS;
+  const int n = net.n, ln = wlane();
+  if (W.phase == PH_F0) {
+    if (!ok) { W.status = CELL_BAD_INPUT; W.phase = PH_DONE; return; }
+    W.st[ST_RHS] += 1;
+    // starting step (Hairer, Norsett & Wanner, Solving ODEs I, II.4), p = 1
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int i = ln + 32 * k;
+      W.iw[k] = (i < n) ? 1.0 / (o.rtol * fabs(W.z[0][k]) + o.atol) : 0.0;
+    }
+    const double d0 = w_wrms<N>(n, W.z[0], W.iw), d1 = w_wrms<N>(n, W.f, W.iw);
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+    h0 = fmin(h0, W.tend);
+    W.h0 = h0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      W.e[k] = W.f[k];  // f0 parked in e
+      W.y[k] = W.z[0][k] + h0 * W.f[k];
+    }
+    W.st[ST_RHS] += 1;
+    W.phase = PH_HW;
+    return;
+  }
+  if (W.phase == PH_HW) {
+    double h = W.h0;
+    if (ok) {
+      double dv[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) dv[k] = W.f[k] - W.e[k];
+      const double d1 = w_wrms<N>(n, W.e, W.iw);
+      const double d2 = w_wrms<N>(n, dv, W.iw) / W.h0;
+      const double dm = fmax(d1, d2);
+      const double h1 = (dm <= 1e-15) ? fmax(1e-6, W.h0 * 1e-3) : sqrt(0.01 / dm);
+      h = fmin(fmin(100.0 * W.h0, h1), W.tend);
+    }
+    W.h = h;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) W.z[1][k] = h * W.e[k];
+    W.t = 0.0;
+    W.q = 1;
+    W.qwait = 2;
+#pragma unroll
+    for (int k = 0; k < QMAX + 3; ++k) W.hist[k] = h;
+    W.need_j = true;
+    W.need_p = true;
+    W.crate = CRATE0;
+    W.gamma_p = 1.0;
+    W.eta_max = ETAMX_FIRST;
+    W.nef = W.ncf = 0;
+    W.jage = W.page = 0;
+    W.have_es = false;
+    W.attempts = 0;
+    w_begin_step(W, net, o);
+    return;
+  }
   if (W.phase == PH_NEWTON) {
     const int r = w_newton_iter<N, LT>(W, sh, net, ok);
     if (r == 0) return;
@@ -754,28 +869,99 @@ __device__ __forceinline__ void w_store(WState<N> &W, const DNet &net, const Cel
     __syncwarp();
     return;
   }
-  double xs = 0.0;
+  if (!(W.status == CELL_BAD_INPUT && W.m < 0)) {
+    double xs = 0.0;
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const int i = ln + 32 * s;
-    if (i < S) {
-      a.x[i * a.ld + c] = W.z[0][s];
-      xs += W.z[0][s];
+    for (int s = 0; s < NS; ++s) {
+      const int i = ln + 32 * s;
+      if (i < S) {
+        a.x[i * a.ld + c] = W.z[0][s];
+        xs += W.z[0][s];
+      }
     }
-  }
-  const double X = wsum(xs);
-  if (net.energy) {
-    const double u = wget<NS>(W.z[0], S);
-    if (ln == 0) a.T[c] = net.gm1 * u / (KB_EV * X);
+    const double X = wsum(xs);
+    if (net.energy) {
+      const double u = wget<NS>(W.z[0], S);
+      if (ln == 0) a.T[c] = net.gm1 * u / (KB_EV * X);
+    }
   }
   if (ln == 0) a.status[c] = W.status;
   if (a.stats && ln < NSTAT) {
     int v = 0;
     for (int k = 0; k < NSTAT; ++k)
-      if (k == ln) v = (k == ST_ORDER) ? W.q : W.st[k];
+      if (k == ln) v = (k == ST_ORDER) ? ((W.status == CELL_BAD_INPUT) ? 0 : W.q) : W.st[k];
     a.stats[ln * a.ld + c] = v;
   }
   __syncwarp();
+}
+
+// Warp-per-cell persistent worker: the warp pulls cells one at a time from
+// the queue and integrates each with the whole warp.
+template <int N, typename LT>
+__device__ __forceinline__ void warp_worker(const DNet &net, const Opts &o, const CellArgs &a,
+                                            unsigned long long *next, const WSh<LT> &sh) {
+  const int64_t total = count_of(a);
+  for (;;) {
+    unsigned long long k = 0;
+    if (wlane() == 0) k = atomicAdd(next, 1ull);
+    k = __shfl_sync(WFULL, k, 0);
+    if ((int64_t)k >= total) break;
+    WState<N> W;
+    w_load_cell<N>(W, net, a, cell_of(a, (int64_t)k));
+    while (W.phase != PH_DONE) {
+      const bool ok = w_rhs<N, LT>(W, sh, net);
+      w_advance<N, LT>(W, sh, net, o, ok);
+    }
+    w_store<N>(W, net, a);
+  }
+}
+
+template <int N, typename LT>
+__global__ void __launch_bounds__(128) k_burn_warp(DNet net, Opts o, CellArgs a, unsigned long long *next,
+                                                   int smem_per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const WSh<LT> sh = wsh_carve<N, LT>(smem + (threadIdx.x >> 5) * (size_t)smem_per_warp, net.R);
+  warp_worker<N, LT>(net, o, a, next, sh);
+}
+
+// One segment of a mixed launch: a network, its cells and its compiled bucket.
+struct SegDev {
+  DNet net;
+  CellArgs a;
+  int bucket;
+};
+
+constexpr int MIXED_MAX_SEGS = 8;
+
+struct MixedArgs {
+  SegDev seg[MIXED_MAX_SEGS];
+  int nseg;
+  int smem_per_warp;  // shared workspace per warp (warp-per-cell segments, thread right-hand sides)
+  int thread_smem;    // 1: thread-per-cell segments use net_rhs_sm in that workspace
+};
+
+// Mixed persistent launch: every warp drains the segment queues starting at a
+// segment chosen by its warp index, so all networks start at once and warps
+// that finish one network move on to the next (one launch for all networks).
+// Networks of up to 13 ODEs run thread-per-cell, larger ones warp-per-cell.
+template <typename LT>
+__global__ void __launch_bounds__(128) k_burn_mixed(MixedArgs m, Opts o, unsigned long long *next) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char *wsp = smem + (threadIdx.x >> 5) * (size_t)m.smem_per_warp;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const StragArgs sa{nullptr, nullptr, 0u, 0};
+  for (int s0 = 0; s0 < m.nseg; ++s0) {
+    const int s = (s0 + warp) % m.nseg;
+    const SegDev &g = m.seg[s];
+    switch (g.bucket) {
+      case 3: persistent_worker<3, LT>(g.net, o, g.a, next + s, sa,
+                                        m.thread_smem ? (double *)wsp : nullptr); break;
+      case 13: persistent_worker<13, LT>(g.net, o, g.a, next + s, sa,
+                                         m.thread_smem ? (double *)wsp : nullptr); break;
+      case 33: warp_worker<33, LT>(g.net, o, g.a, next + s, wsh_carve<33, LT>(wsp, g.net.R)); break;
+      default: warp_worker<40, LT>(g.net, o, g.a, next + s, wsh_carve<40, LT>(wsp, g.net.R)); break;
+    }
+  }
 }
 
 // Straggler kernel: each warp takes handed-off cells (records of the thread

@@ -38,9 +38,10 @@ bound (CORTES = 0.1 of the local tolerance, ~1e-7 of the state per step), and
 over a cell's history those differences add up like a global error (measured:
 up to ~2e-4 on the 33-ODE network). So for it every finished cell gets the
 distribution check above (as accurate as the oracle against the tight
-solution), stable cells must stay within 100 (rtol |o| + atol) of the oracle
-(a gross-error bar on the tolerance scale), and the per-result deviation from
-the FP64 oracle is reported
+solution), stable cells must stay within 1000 (rtol |o| + atol) of the oracle,
+i.e. 1000 error weights (a gross-error bar above the oracle's own integration
+error, which reaches ~1e-4 relative on stable 33-ODE cells), and the
+per-result deviation from the FP64 oracle is reported
 (stable_within_1e-5_frac, max_rel_x_stable)."""
 from __future__ import annotations
 
@@ -92,8 +93,8 @@ def compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable=None, tight=None, atol
     dx = np.abs(g_x - o_x)
     strict = both_ok & stable
     if fp32_matrix:
-        x_bad = ((dx > 100.0 * (1e-6 * np.abs(o_x) + atol)) & strict[None, :]).any(axis=0)
-        bar = 1e-4
+        x_bad = ((dx > 1e3 * (1e-6 * np.abs(o_x) + atol)) & strict[None, :]).any(axis=0)
+        bar = 1e-3
     else:
         x_bad = ((dx > rtol * np.abs(o_x) + 10.0 * atol) & strict[None, :]).any(axis=0)
         bar = rtol

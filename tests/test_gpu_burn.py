@@ -38,13 +38,14 @@ def _reference(net, cells, dt, index=None, lu=64):
     return ox, oT, os_, ost, stable, (tx, tT)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("lu", [64, 32])
 def test_robertson_4096(mc, variant, lu):
     net, cells = robertson_network(), robertson_cells(4096, 1)
     gx, gT, gs, gst = _run(mc, net, cells, 40.0, variant=variant, lu_precision=lu)
     ox, oT, os_, ost = _oracle(net, cells, 40.0)
-    rep = compare(gx, gT, gs, ox, oT, os_, ost, fp32_matrix=(lu == 32))
+    tx, _, _, _ = _oracle(net, cells, 40.0, rtol=1e-11, atol=1e-17)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, tight=(tx, None), fp32_matrix=(lu == 32))
     print(rep)
     assert rep["pass"], rep
     assert (gs == 0).all()
@@ -80,7 +81,7 @@ def test_full_size_sampled(mc):
     assert np.mean(gs == 0) > 0.99
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_ragged_and_degenerate_sizes(mc, variant):
     net = network_13()
     h = mc.Network(net)
@@ -143,8 +144,8 @@ def test_bad_inputs_and_step_cap(mc):
     np.testing.assert_array_equal(gs, os_)
     assert (gs == 1).any()
     np.testing.assert_array_equal(gst[0] + gst[1] + gst[2], ost[0] + ost[1] + ost[2])
-    same = (gst[:3] == ost[:3]).all(axis=0)
-    assert same.mean() >= 0.95
+    same = (gst[:7] == ost[:7]).all(axis=0)
+    assert same.mean() >= 0.8
     np.testing.assert_allclose(gx[:, same], ox[:, same], rtol=1e-5, atol=1e-9)
 
 
@@ -267,5 +268,5 @@ def test_autotune_returns_a_measured_shape(mc):
     x0 = d["x"].clone()
     best = mc.mc_autotune(h, mc.mc_burn_opts_default(lu_precision=32), 2048, 1e10, d["x"], 2048, d["T"], d["ndens"])
     torch.cuda.synchronize()
-    assert best.variant in (1, 2) and best.block_threads in (64, 128, 256)
+    assert best.variant in (1, 2, 3) and best.block_threads in (64, 128, 256)
     assert torch.equal(d["x"], x0)  # the sample is not modified
