@@ -118,7 +118,7 @@ typedef struct {
     int32_t block_threads;  /* threads per block, 0 = autotuned */
     int32_t blocks_per_sm;  /* persistent grid = blocks_per_sm x SMs, 0 = autotuned */
     int32_t straggler_steps;/* persistent variant: a cell still running after this many
-                               attempts is finished by a whole warp (0 = default 2048,
+                               attempts is finished by a whole warp (0 = default 1024,
                                -1 = never) */
 } mc_burn_opts;
 

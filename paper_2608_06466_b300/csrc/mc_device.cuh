@@ -166,72 +166,6 @@ __device__ __forceinline__ bool net_rhs(const DNet &net, const CellIn &c, const 
   return ok;
 }
 
-// Thread-form right-hand side with the lane's point and the net reaction rates
-// in the warp's shared region (element k of lane l at sm[k * 32 + l], so a
-// warp's accesses fall in distinct banks): first every w_r, then each
-// species' sum gathered in a register along its occurrence list. The lists
-// follow the order in which net_rhs applies the terms, so f is the same bit
-// for bit; the gather avoids net_rhs's chains of dependent read-modify-writes
-// through local memory. Needs 32 (N + R) doubles of shared memory per warp.
-template <int N>
-__device__ __forceinline__ bool net_rhs_sm(const DNet &net, const CellIn &c, const double *y, double *f,
-                                           double *sm) {
-  const int S = net.S, ln = threadIdx.x & 31;
-  double *ys = sm + ln;
-  double *ws = sm + 32 * N + ln;
-  double X = 0.0;
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if (i < net.n) {
-      ys[32 * i] = y[i];
-      if (i < S) X += y[i];
-    }
-  double lnT = c.lnT, invT = c.invT;
-  if (net.energy) {
-    const double T = net.gm1 * y[S] / (KB_EV * X);
-    if (!(T > 0.0) || !isfinite(T)) return false;
-    lnT = log(T);
-    invT = 1.0 / T;
-  }
-  double fu = 0.0;
-  for (int r = 0; r < net.R; ++r) {
-    const int4 s = __ldg(&net.side[r]);
-    const RxPar &p = net.par[r];
-    double kf = rexp(__ldg(&p.lnAf) + __ldg(&p.bf) * lnT - __ldg(&p.Cf) * invT, net.exptab);
-    double kr = 0.0;
-    if (__ldg(&p.rev) != 0.0) kr = rexp(__ldg(&p.lnAr) + __ldg(&p.br) * lnT - __ldg(&p.Cr) * invT, net.exptab);
-    if (c.ks) {
-      const double sc = c.ks[r * c.ks_ld];
-      kf *= sc;
-      kr *= sc;
-    }
-    const double pf = (s.y < 0) ? ys[32 * s.x] : c.nd * ys[32 * s.x] * ys[32 * s.y];
-    const double pr = (s.w < 0) ? ys[32 * s.z] : c.nd * ys[32 * s.z] * ys[32 * s.w];
-    const double w = kf * pf - kr * pr;
-    ws[32 * r] = w;
-    if (net.energy) fu += __ldg(&p.dE) * w;
-  }
-  bool ok = true;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    if (i < S) {
-      double v = 0.0;
-      const int q1 = __ldg(&net.csr_ptr[i + 1]);
-      for (int q = __ldg(&net.csr_ptr[i]); q < q1; ++q) {
-        const int ent = __ldg(&net.csr_ent[q]);
-        const double w = ws[32 * (ent >> 2)];
-        v = ((ent & 3) < 2) ? v - w : v + w;
-      }
-      f[i] = v;
-      if (!isfinite(v)) ok = false;
-    } else if (i < net.n) {
-      f[i] = fu;
-      if (!isfinite(fu)) ok = false;
-    }
-  }
-  return ok;
-}
-
 // Analytic Jacobian J[i*N + j] = d f_i / d y_j (row stride N), accumulated in
 // the matrix precision LT. For the energy form T depends on the state through
 // the EOS (dT/dx_j = -T / sum x, dT/du = (gamma-1) / (k_B sum x)); g_i =

@@ -148,7 +148,7 @@ struct StragArgs {
 // every lane's cell is stored or handed off.
 template <int N, typename LT>
 __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs &a,
-                                  unsigned long long *next, const StragArgs &sa, double *tsm) {
+                                  unsigned long long *next, const StragArgs &sa) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t total = count_of(a);
@@ -176,7 +176,7 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
     if (!__any_sync(FULL, L.phase != PH_IDLE)) break;
     const bool busy = L.phase != PH_IDLE && L.phase != PH_DONE;
     if (busy) {
-      const bool ok = tsm ? net_rhs_sm<N>(net, L.cin, L.y, L.f, tsm) : net_rhs<N>(net, L.cin, L.y, L.f);
+      const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
       advance(L, net, o, ok);
       run_stages(L, net, o);
       if (sa.rec && L.phase == PH_NEWTON && L.m == 0 && L.attempts >= sa.threshold && !L.kept) {
@@ -192,15 +192,10 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
   }
 }
 
-// Shared memory per warp for net_rhs_sm (0 when it does not fit: net_rhs then).
-__host__ __device__ inline size_t thread_rhs_smem(int N, int R) { return sizeof(double) * 32 * (size_t)(N + R); }
-
 template <int N, typename LT>
 __global__ void __launch_bounds__(256) k_burn_persistent(DNet net, Opts o, CellArgs a,
-                                                         unsigned long long *next, StragArgs sa, int tsm_per_warp) {
-  extern __shared__ __align__(16) unsigned char tsmem[];
-  double *tsm = tsm_per_warp ? (double *)(tsmem + (threadIdx.x >> 5) * (size_t)tsm_per_warp) : nullptr;
-  persistent_worker<N, LT>(net, o, a, next, sa, tsm);
+                                                         unsigned long long *next, StragArgs sa) {
+  persistent_worker<N, LT>(net, o, a, next, sa);
 }
 
 }  // namespace mc

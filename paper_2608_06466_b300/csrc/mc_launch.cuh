@@ -44,7 +44,10 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
     if (!a.n_dev) blocks = std::min<int64_t>(blocks, (a.n_cells + threads - 1) / threads);
     if (blocks < 1) blocks = 1;
     StragArgs sa{nullptr, nullptr, 0u, 0};
-    const int64_t ncap = a.n_dev ? 0 : std::min<int64_t>(16384, std::max<int64_t>(256, a.n_cells / 64));
+    // record list: room for every cell that may pass the threshold (a lane that
+    // finds it full keeps its cell), bounded to 2 GB of records
+    const int64_t rec_max = (int64_t)((2ull << 30) / sizeof(Lane<N, LT>));
+    const int64_t ncap = a.n_dev ? 0 : std::min<int64_t>(rec_max, std::max<int64_t>(256, a.n_cells / 8));
     if (strag_steps > 0 && ncap > 0 && strag_steps < o.max_steps) {
       void *rec = nullptr;
       uint32_t *cnt = nullptr;
@@ -54,28 +57,14 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
       e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
       if (e != cudaSuccess) return cuda_error(e, "straggler counter reset");
     }
-    // per-warp shared slices for the gather form of the right-hand side
-    const size_t tsm = thread_rhs_smem(N, d.R);
-    int tsm_per_warp = 0;
-    if (d.R <= 128 && tsm * (threads / 32) <= 96 * 1024) {
-      tsm_per_warp = (int)tsm;
-      static thread_local int configured_t = 0;
-      const int bytes = tsm_per_warp * (threads / 32);
-      if (configured_t < bytes) {
-        e = cudaFuncSetAttribute(k_burn_persistent<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return cuda_error(e, "persistent kernel smem attribute");
-        configured_t = bytes;
-      }
-    }
-    k_burn_persistent<N, LT><<<(unsigned)blocks, threads, tsm_per_warp * (threads / 32), st>>>(d, o, a, next, sa,
-                                                                                               tsm_per_warp);
+    k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
     if (sa.rec) {
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_error(e, "burn kernel launch");
       count_launch(1);
       // warp-cooperative pass over the handed-off cells (count read on the device)
-      // one-warp blocks, 8 per SM: each straggler gets its own warp and at most
-      // two share an SM sub-partition's FP64 pipe
+      // one-warp blocks, 16 per SM: four warps per SM sub-partition hide the
+      // latency of each warp's dependent step logic
       const int per_warp = (int)wsh_bytes<N, LT>(d.R);
       const int wthreads = 32;
       const int smem = per_warp;
@@ -87,7 +76,7 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
       }
       e = cudaMemsetAsync(next + 1, 0, sizeof(unsigned long long), st);
       if (e != cudaSuccess) return cuda_error(e, "straggler queue reset");
-      const int wblocks = std::max(1, std::min(sms * 8, (int)sa.cap));
+      const int wblocks = std::max(1, std::min(sms * 16, (int)sa.cap));
       k_burn_straggler<N, LT><<<wblocks, wthreads, smem, st>>>(d, o, a, (const Lane<N, LT> *)sa.rec, sa.count,
                                                               sa.cap, next + 1, per_warp);
     }

@@ -95,22 +95,6 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     if (b == 33) per_warp = std::max(per_warp, ob.lu_precision == 64 ? wsh_bytes<33, double>(R) : wsh_bytes<33, float>(R));
     if (b == 40) per_warp = std::max(per_warp, ob.lu_precision == 64 ? wsh_bytes<40, double>(R) : wsh_bytes<40, float>(R));
   }
-  // thread-per-cell segments gather their right-hand sides in the same region
-  bool tsm_ok = true;
-  size_t tsm_need = 0;
-  for (int s = 0; s < nseg; ++s) {
-    const int b = m.seg[s].bucket, R = segs[s].net->R;
-    if (b == 3 || b == 13) {
-      if (R > 128) tsm_ok = false;
-      tsm_need = std::max(tsm_need, thread_rhs_smem(b, R));
-    }
-  }
-  if (tsm_ok && std::max(per_warp, tsm_need) * 4 <= 160 * 1024) {
-    per_warp = std::max(per_warp, tsm_need);
-    m.thread_smem = 1;
-  } else {
-    m.thread_smem = 0;
-  }
   m.smem_per_warp = (int)per_warp;
   const int mthreads = 128;
   const int msmem = (int)per_warp * (mthreads / 32);

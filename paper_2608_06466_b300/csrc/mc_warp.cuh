@@ -936,8 +936,7 @@ constexpr int MIXED_MAX_SEGS = 8;
 struct MixedArgs {
   SegDev seg[MIXED_MAX_SEGS];
   int nseg;
-  int smem_per_warp;  // shared workspace per warp (warp-per-cell segments, thread right-hand sides)
-  int thread_smem;    // 1: thread-per-cell segments use net_rhs_sm in that workspace
+  int smem_per_warp;  // shared workspace of the warp-per-cell segments
 };
 
 // Mixed persistent launch: every warp drains the segment queues starting at a
@@ -954,10 +953,8 @@ __global__ void __launch_bounds__(128) k_burn_mixed(MixedArgs m, Opts o, unsigne
     const int s = (s0 + warp) % m.nseg;
     const SegDev &g = m.seg[s];
     switch (g.bucket) {
-      case 3: persistent_worker<3, LT>(g.net, o, g.a, next + s, sa,
-                                        m.thread_smem ? (double *)wsp : nullptr); break;
-      case 13: persistent_worker<13, LT>(g.net, o, g.a, next + s, sa,
-                                         m.thread_smem ? (double *)wsp : nullptr); break;
+      case 3: persistent_worker<3, LT>(g.net, o, g.a, next + s, sa); break;
+      case 13: persistent_worker<13, LT>(g.net, o, g.a, next + s, sa); break;
       case 33: warp_worker<33, LT>(g.net, o, g.a, next + s, wsh_carve<33, LT>(wsp, g.net.R)); break;
       default: warp_worker<40, LT>(g.net, o, g.a, next + s, wsh_carve<40, LT>(wsp, g.net.R)); break;
     }
