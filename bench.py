@@ -110,11 +110,11 @@ def cpu_baseline(net, n_sample, seed):
             "ok_fraction": float(np.mean(status == 0))}
 
 
-def serving_measurement(mc, n_sat=6, n_load=8, seed=7):
-    """Serving loop on AMR-box requests (edge L log-uniform in [16, 128], cells
+def serving_measurement(mc, n_sat=6, n_load=8, seed=7, edge_range=(16, 64)):
+    """Serving loop on AMR-box requests (edge L log-uniform in edge_range, cells
     = L^3, 50/50 net13 / net33, FP32-matrix path, 150 GB budget): closed-loop
     saturation, then Poisson arrivals at 0.5x and 0.9x of it. Bounded request
-    counts keep the run within minutes."""
+    counts and box sizes keep the run within minutes."""
     import time as _t
     from mc_inputs import box_request_stream, network_13, network_33, synthetic_cells
     nets = {"net13": network_13(), "net33": network_33()}
@@ -145,17 +145,18 @@ def serving_measurement(mc, n_sat=6, n_load=8, seed=7):
         cells = sum(b[1] for b in bufs)
         return lat, cells, span, sum(i.n_failed for i in infos)
 
-    sat_reqs = box_request_stream(n_sat, 1.0, seed=seed)
+    sat_reqs = box_request_stream(n_sat, 1.0, seed=seed, edge_range=edge_range)
     lat, cells, span, _ = run(sat_reqs, [0.0] * n_sat)
     lam_cells = cells / span
-    sizes = np.array([r["n_cells"] for r in box_request_stream(4096, 1.0, seed=seed + 1)])
+    sizes = np.array([r["n_cells"] for r in box_request_stream(4096, 1.0, seed=seed + 1, edge_range=edge_range)])
     mean_cells = float(sizes.mean())
     out = {"lambda_sat_cells_per_s": lam_cells, "mean_cells_per_request": mean_cells,
+           "edge_range": list(edge_range),
            "saturation_requests": n_sat, "loads": [],
            "note": f"{n_load} Poisson requests per load level (bounded so the run ends in minutes)"}
     for load in (0.5, 0.9):
         rate = load * lam_cells / mean_cells
-        reqs = box_request_stream(n_load, rate, seed=seed + int(load * 100))
+        reqs = box_request_stream(n_load, rate, seed=seed + int(load * 100), edge_range=edge_range)
         arrivals = [r["t_arrive"] for r in reqs]
         lat, cells, span, failed = run(reqs, arrivals)
         out["loads"].append({"load": load, "requests": n_load, "rate_req_per_s": rate,
@@ -199,7 +200,9 @@ def main():
     ap.add_argument("--cells", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="add the serving-loop measurement (AMR-box requests, a few minutes)")
+    ap.add_argument("--no-serving", action="store_true", help="no serving measurement (the default)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -332,12 +335,12 @@ def main():
                   "stable_within_1e-5_frac": rep["stable_within_1e-5_frac"]}
 
     serving = None
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and args.serving and not args.no_serving:
         serving = serving_measurement(mc)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(net, int(os.environ.get("MC_CPU_SAMPLE", "32768")), CELL_SEED)
+        cpu = cpu_baseline(net, int(os.environ.get("MC_CPU_SAMPLE", "262144")), CELL_SEED)
 
     if rank == 0:
         achieved = 2 * ops / (ms32 / 1e3) / 1e12
@@ -349,7 +352,7 @@ def main():
                                    "(13 ODEs), 40 reversible reactions, ideal gas gamma=5/3",
                        "n_cells_per_gpu": n, "dt_s": DT, "rtol": 1e-6, "atol": 1e-10,
                        "T_K": "log-uniform [10, 1e4]", "n_cm3": "log-uniform [1, 1e8]",
-                       "lu_precision": 32, "variant": "persistent", "max_steps": 100000,
+                       "lu_precision": 32, "variant": "persistent (cost-ordered queue, one cooperative launch with hand-off)", "max_steps": 100000,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"independent shards x{world}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak, "traffic": None,

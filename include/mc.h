@@ -118,7 +118,7 @@ typedef struct {
     int32_t block_threads;  /* threads per block, 0 = autotuned */
     int32_t blocks_per_sm;  /* persistent grid = blocks_per_sm x SMs, 0 = autotuned */
     int32_t straggler_steps;/* persistent variant: a cell still running after this many
-                               attempts is finished by a whole warp (0 = default 1024,
+                               attempts is finished by a whole warp (0 = default 2048,
                                -1 = never) */
 } mc_burn_opts;
 
@@ -142,7 +142,12 @@ int32_t mc_network_n_ode(const mc_network *net);
  *   stream     cudaStream_t or NULL
  * ld >= n_cells. Device pointers: asynchronous, returns after the launch.
  * Host pointers (all cell arrays on the host): synchronous round trip through
- * library device memory. Errors: MC_E_INVALID, MC_E_NOMEM, MC_E_CUDA. */
+ * library device memory. Errors: MC_E_INVALID, MC_E_NOMEM, MC_E_CUDA.
+ * Queue-fed variants (persistent, warp) hand the cells out in decreasing order
+ * of a cost key (dt times the error-weighted norm of f at the start): a cell's
+ * result does not depend on that order. With 128-thread blocks the persistent
+ * variant runs as one cooperative launch in which warps whose queue is drained
+ * finish the handed-off cells while the rest of the bulk still runs. */
 mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
                         double dt, double *x, int64_t ld, double *T, const double *ndens,
                         const double *rate_scale, int32_t *status, int32_t *stats,

@@ -54,7 +54,7 @@ void load_cache() {
                     "{\"device\": \"%255[^\"]\", \"n\": %d, \"R\": %d, \"energy\": %d, \"lu\": %d, "
                     "\"variant\": %d, \"threads\": %d, \"blocks_per_sm\": %d}",
                     dev, &n, &R, &en, &lu, &var, &thr, &bps) == 8)
-      g_table[Key(dev, n, R, en, lu)] = Tuned{var, thr, bps, 1024};
+      g_table[Key(dev, n, R, en, lu)] = Tuned{var, thr, bps, 2048};
   }
   std::fclose(f);
 }
@@ -76,7 +76,7 @@ void save_entry(const Key &k, const Tuned &t) {
 Tuned mc::autotune_pick(const mc_network *net, const mc_burn_opts &o) {
   // defaults: thread-per-cell with hand-off for small networks, warp-per-cell
   // above 16 ODEs (the per-cell matrices no longer fit a lane's share of L1)
-  Tuned t{(net && net->n > 16) ? MC_VARIANT_WARP : MC_VARIANT_PERSISTENT, 128, 2, 1024};
+  Tuned t{(net && net->n > 16) ? MC_VARIANT_WARP : MC_VARIANT_PERSISTENT, 128, 2, 2048};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();
@@ -158,7 +158,7 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
   cudaFree(ws);
   if (s != MC_OK) return s;
   if (e != cudaSuccess) return cuda_error(e, "autotune trial");
-  Tuned t{win.var, win.thr, win.bps ? win.bps : 1, 1024};
+  Tuned t{win.var, win.thr, win.bps ? win.bps : 1, 2048};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();

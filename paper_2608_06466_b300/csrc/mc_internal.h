@@ -69,4 +69,14 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
 // claim counter, on the current device.
 mc_status straggler_scratch(size_t bytes, void **rec, uint32_t **count);
 
+// Library-owned cost-order buffers for n cells on device dev, scratch set of
+// the current stream: the queue's cell list, one bucket byte per cell and the
+// bucket histogram.
+mc_status order_scratch(int dev, int64_t n, int32_t **index, uint8_t **bkt, uint32_t **hist);
+
+// Write into index the cells 0..a.n_cells-1 ordered by decreasing cost key
+// (mc_order.cu); four operations on stream st, no host synchronisation.
+mc_status order_cells(const mc_network *net, const Opts &o, const CellArgs &a, int32_t *index, uint8_t *bkt,
+                      uint32_t *hist, cudaStream_t st);
+
 }  // namespace mc

@@ -140,7 +140,26 @@ struct StragArgs {
   uint32_t *count;     // records claimed (may exceed cap; only cap are written)
   uint32_t cap;
   int threshold;
+  uint32_t *flag;      // per record: 0 not yet written, 1 written, 2 integrated
 };
+
+// Relaxed loads for polling: unlike an acquire they leave the SM's L1 (which
+// holds the spilled lane state of the thread-form workers) untouched.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
 
 // Persistent worker loop over one queue of cells. `next` counts cells handed
 // out (reset to 0 before the launch). Every lane of the warp runs the loop, so
@@ -183,6 +202,7 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
         const uint32_t k = atomicAdd(sa.count, 1u);
         if (k < sa.cap) {
           static_cast<Lane<N, LT> *>(sa.rec)[k] = L;
+          if (sa.flag) st_release(&sa.flag[k], 1u);  // record k is complete
           L.phase = PH_IDLE;
         } else {
           L.kept = true;
@@ -196,6 +216,80 @@ template <int N, typename LT>
 __global__ void __launch_bounds__(256) k_burn_persistent(DNet net, Opts o, CellArgs a,
                                                          unsigned long long *next, StragArgs sa) {
   persistent_worker<N, LT>(net, o, a, next, sa);
+}
+
+// ---- cost order of the cell queue -------------------------------------------
+// A cell's result does not depend on where it sits in the queue (each cell is
+// integrated on its own, and the hand-off happens at a fixed attempt count), so
+// the queue may hand out expensive cells first: the drain at the end of a
+// persistent launch then holds cheap cells only, and long cells reach the
+// hand-off early. The cost key is dt times the weighted RMS norm of f(y0) with
+// the error-test weights 1/(rtol |y0_i| + atol) -- the number of the cell's
+// natural time scales in the step, the quantity the starting-step rule
+// (Hairer, Norsett & Wanner, Solving ODEs I, II.4) begins from. Keys are
+// grouped in half-octaves; bucket 0 is the most expensive.
+constexpr int ORDER_BUCKETS = 256;
+constexpr int ORDER_CHUNK = 4096;  // cells per block of the scatter kernel
+
+template <int N>
+__device__ int cost_bucket(const DNet &net, const Opts &o, const CellArgs &a, int64_t c) {
+  const int S = net.S, n = net.n;
+  double y[N], f[N];
+  bool good = true;
+  double X = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double v = (i < S) ? a.x[i * a.ld + c] : 0.0;
+    y[i] = v;
+    if (i < S) {
+      X += v;
+      if (!isfinite(v)) good = false;
+    }
+  }
+  CellIn cin;
+  cin.nd = a.nd ? a.nd[c] : 1.0;
+  const double T = a.T ? a.T[c] : 1.0;
+  if (!(cin.nd > 0.0) || !isfinite(cin.nd) || !(T > 0.0) || !isfinite(T)) good = false;
+  cin.ks = a.ks ? a.ks + c : nullptr;
+  cin.ks_ld = a.ld;
+  cin.lnT = 0.0;
+  cin.invT = 0.0;
+  if (net.energy) {
+    if (!(X > 0.0) || !isfinite(X)) good = false;
+    if (S < N) y[S] = X * KB_EV * T / net.gm1;
+  } else if (good) {
+    cin.lnT = log(T);
+    cin.invT = 1.0 / T;
+  }
+  if (!good || !net_rhs<N>(net, cin, y, f)) return ORDER_BUCKETS - 1;
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) {
+      const double w = f[i] / (o.rtol * fabs(y[i]) + o.atol);
+      s += w * w;
+    }
+  const double k = sqrt(s / n) * a.dt;
+  if (!(k > 1.0)) return ORDER_BUCKETS - 2;  // less than one time scale (or not a number)
+  const int lv = (int)(2.0f * log2f((float)fmin(k, 1e38)));
+  return max(0, ORDER_BUCKETS - 3 - lv);
+}
+
+// Bucket of every cell (bkt[c]) and the bucket histogram (hist, zeroed first).
+template <int N>
+__global__ void __launch_bounds__(256) k_order_key(DNet net, Opts o, CellArgs a, uint8_t *bkt, uint32_t *hist) {
+  __shared__ uint32_t h[ORDER_BUCKETS];
+  for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n_cells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int b = cost_bucket<N>(net, o, a, c);
+    bkt[c] = (uint8_t)b;
+    atomicAdd(&h[b], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
 }  // namespace mc

@@ -43,29 +43,73 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
     int64_t blocks = (int64_t)sms * blocks_per_sm;
     if (!a.n_dev) blocks = std::min<int64_t>(blocks, (a.n_cells + threads - 1) / threads);
     if (blocks < 1) blocks = 1;
-    StragArgs sa{nullptr, nullptr, 0u, 0};
+    StragArgs sa{nullptr, nullptr, 0u, 0, nullptr};
     // record list: room for every cell that may pass the threshold (a lane that
-    // finds it full keeps its cell), bounded to 2 GB of records
+    // finds it full keeps its cell), bounded to 2 GB of records; a flag per
+    // record follows the records
     const int64_t rec_max = (int64_t)((2ull << 30) / sizeof(Lane<N, LT>));
     const int64_t ncap = a.n_dev ? 0 : std::min<int64_t>(rec_max, std::max<int64_t>(256, a.n_cells / 8));
     if (strag_steps > 0 && ncap > 0 && strag_steps < o.max_steps) {
       void *rec = nullptr;
       uint32_t *cnt = nullptr;
-      mc_status s = straggler_scratch(sizeof(Lane<N, LT>) * (size_t)ncap, &rec, &cnt);
+      const size_t rbytes = (sizeof(Lane<N, LT>) * (size_t)ncap + 255) & ~(size_t)255;
+      mc_status s = straggler_scratch(rbytes + sizeof(uint32_t) * (size_t)ncap, &rec, &cnt);
       if (s != MC_OK) return s;
-      sa = StragArgs{rec, cnt, (uint32_t)ncap, strag_steps};
-      e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
-      if (e != cudaSuccess) return cuda_error(e, "straggler counter reset");
+      sa = StragArgs{rec, cnt, (uint32_t)ncap, strag_steps, (uint32_t *)((char *)rec + rbytes)};
+      // cnt[0] records, cnt[1] fused claims, cnt[2] finished bulk warps
+      e = cudaMemsetAsync(cnt, 0, 4 * sizeof(uint32_t), st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(sa.flag, 0, sizeof(uint32_t) * (size_t)ncap, st);
+      if (e != cudaSuccess) return cuda_error(e, "straggler list reset");
     }
-    k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
-    if (sa.rec) {
+    if (!sa.rec) {
+      k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
+    } else {
+      const int per_warp = (int)wsh_bytes<N, LT>(d.R);
+      bool fused = false;
+      if (threads == 128) {
+        // one cooperative launch (every block resident): warps whose queue is
+        // drained integrate the records while the rest of the bulk still runs
+        const int fsmem = per_warp * 4;
+        static thread_local int configured_f = 0;
+        e = cudaSuccess;
+        if (configured_f < fsmem) {
+          e = cudaFuncSetAttribute(k_burn_fused<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem);
+          // shared-memory carveout just large enough for the resident blocks: the
+          // rest stays L1, which caches the thread-form lanes' spilled state
+          int smem_sm = 0;
+          if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+          if (e == cudaSuccess && smem_sm > 0) {
+            const int pct = std::min(100, (int)((100LL * fsmem * blocks_per_sm + smem_sm - 1) / smem_sm) + 1);
+            e = cudaFuncSetAttribute(k_burn_fused<N, LT>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+          }
+          if (e == cudaSuccess) configured_f = fsmem;
+        }
+        int per_sm = 0;
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_burn_fused<N, LT>, 128, fsmem);
+        if (e != cudaSuccess) return cuda_error(e, "fused kernel set-up");
+        if ((int64_t)per_sm * sms >= blocks) {
+          DNet dd = d;
+          Opts oo = o;
+          CellArgs aa = a;
+          unsigned long long *nx = next;
+          FuseArgs fa{sa.count + 1, sa.count + 2, (uint32_t)(blocks * 4)};
+          int pw = per_warp;
+          void *args[] = {&dd, &oo, &aa, &nx, &sa, &fa, &pw};
+          e = cudaLaunchCooperativeKernel((const void *)k_burn_fused<N, LT>, dim3((unsigned)blocks), dim3(128), args,
+                                          (size_t)fsmem, st);
+          if (e != cudaSuccess) return cuda_error(e, "fused burn launch");
+          fused = true;
+        }
+      }
+      if (!fused) k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_error(e, "burn kernel launch");
       count_launch(1);
-      // warp-cooperative pass over the handed-off cells (count read on the device)
-      // one-warp blocks, 16 per SM: four warps per SM sub-partition hide the
-      // latency of each warp's dependent step logic
-      const int per_warp = (int)wsh_bytes<N, LT>(d.R);
+      // warp-cooperative pass over the handed-off cells not yet integrated
+      // (count and flags read on the device); one-warp blocks, 16 per SM: four
+      // warps per SM sub-partition hide the latency of each warp's dependent
+      // step logic
       const int wthreads = 32;
       const int smem = per_warp;
       static thread_local int configured = 0;
@@ -78,7 +122,7 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
       if (e != cudaSuccess) return cuda_error(e, "straggler queue reset");
       const int wblocks = std::max(1, std::min(sms * 16, (int)sa.cap));
       k_burn_straggler<N, LT><<<wblocks, wthreads, smem, st>>>(d, o, a, (const Lane<N, LT> *)sa.rec, sa.count,
-                                                              sa.cap, next + 1, per_warp);
+                                                              sa.cap, sa.flag, next + 1, per_warp);
     }
   }
   e = cudaGetLastError();

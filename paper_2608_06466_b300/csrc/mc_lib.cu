@@ -183,6 +183,8 @@ struct DevScratch {
   void *rec = nullptr;                  // straggler records
   uint32_t *rec_count = nullptr;
   size_t rec_bytes = 0;
+  void *order = nullptr;                // cost order: list, bucket bytes, histogram
+  int64_t order_cap = 0;
 };
 std::mutex g_scratch_mu;
 std::map<std::pair<int, uintptr_t>, DevScratch> g_scratch;
@@ -222,6 +224,7 @@ void mc::scratch_free(void *h) {
   cudaFree(d->retry);
   cudaFree(d->rec);
   cudaFree(d->rec_count);
+  cudaFree(d->order);
   delete d;
 }
 
@@ -272,6 +275,29 @@ mc_status mc::straggler_scratch(size_t bytes, void **rec, uint32_t **count) {
   }
   *rec = s.rec;
   *count = s.rec_count;
+  return MC_OK;
+}
+
+mc_status mc::order_scratch(int dev, int64_t n, int32_t **index, uint8_t **bkt, uint32_t **hist) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  DevScratch &s = scratch_of(dev);
+  const size_t list = ((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255;
+  const size_t bytes = ((size_t)n + 255) & ~(size_t)255;
+  if (n > s.order_cap) {
+    cudaError_t e = retire(s.order);
+    s.order = nullptr;
+    s.order_cap = 0;
+    if (e != cudaSuccess) return cuda_error(e, "order grow sync");
+    e = cudaMalloc(&s.order, list + bytes + sizeof(uint32_t) * ORDER_BUCKETS);
+    if (e != cudaSuccess) return cuda_error(e, "order buffer allocation");
+    s.order_cap = n;
+  }
+  // the layout follows the capacity, so a smaller n reuses the same offsets
+  const size_t cl = ((size_t)s.order_cap * sizeof(int32_t) + 255) & ~(size_t)255;
+  const size_t cb = ((size_t)s.order_cap + 255) & ~(size_t)255;
+  *index = (int32_t *)s.order;
+  *bkt = (uint8_t *)s.order + cl;
+  *hist = (uint32_t *)((uint8_t *)s.order + cl + cb);
   return MC_OK;
 }
 
@@ -361,7 +387,19 @@ mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const C
   int32_t *retry;
   mc_status s = scratch_get(dev, ob.lu_precision == 32 ? a0.n_cells : 0, &next, &rcount, &retry);
   if (s != MC_OK) return s;
-  return burn_device_scratch(net, ob, a0, st, next, rcount, retry, true);
+  // queue-fed launches hand out the cells in decreasing cost order
+  CellArgs a = a0;
+  if (!a0.index && !a0.n_dev && autotune_pick(net, ob).variant != MC_VARIANT_PLAIN) {
+    int32_t *order;
+    uint8_t *bkt;
+    uint32_t *hist;
+    s = order_scratch(dev, a0.n_cells, &order, &bkt, &hist);
+    if (s != MC_OK) return s;
+    s = order_cells(net, Opts{ob.rtol, ob.atol, ob.max_order, ob.max_steps}, a0, order, bkt, hist, st);
+    if (s != MC_OK) return s;
+    a.index = order;
+  }
+  return burn_device_scratch(net, ob, a, st, next, rcount, retry, true);
 }
 
 // Shared argument checks of the batch entry points. *on_dev tells whether the

@@ -962,19 +962,25 @@ __global__ void __launch_bounds__(128) k_burn_mixed(MixedArgs m, Opts o, unsigne
 }
 
 // Straggler kernel: each warp takes handed-off cells (records of the thread
-// form's state) until the list is done; count is read on the device.
+// form's state) until the list is done; count is read on the device. After a
+// fused launch it integrates only the records that launch left (flag != 2).
 template <int N, typename LT>
 __global__ void __launch_bounds__(128) k_burn_straggler(DNet net, Opts o, CellArgs a, const Lane<N, LT> *rec,
-                                                        const uint32_t *count, uint32_t cap,
+                                                        const uint32_t *count, uint32_t cap, const uint32_t *flag,
                                                         unsigned long long *next, int smem_per_warp) {
   extern __shared__ __align__(16) unsigned char smem[];
   const WSh<LT> sh = wsh_carve<N, LT>(smem + (threadIdx.x >> 5) * (size_t)smem_per_warp, net.R);
   const uint32_t total = min(*count, cap);
   for (;;) {
     unsigned long long k = 0;
-    if (wlane() == 0) k = atomicAdd(next, 1ull);
+    int skip = 0;
+    if (wlane() == 0) {
+      k = atomicAdd(next, 1ull);
+      skip = (k < total && flag && flag[k] == 2u) ? 1 : 0;
+    }
     k = __shfl_sync(WFULL, k, 0);
     if (k >= total) break;
+    if (__shfl_sync(WFULL, skip, 0)) continue;
     WState<N> W;
     w_load<N, LT>(W, rec[k], sh, net);
     while (W.phase != PH_DONE) {
@@ -983,6 +989,95 @@ __global__ void __launch_bounds__(128) k_burn_straggler(DNet net, Opts o, CellAr
     }
     w_store<N>(W, net, a);
   }
+}
+
+// ---- fused launch: bulk and hand-off in one grid -----------------------------
+// Every warp first runs the thread-per-cell queue; once its queue is drained it
+// integrates handed-off records warp-per-cell while other warps are still in
+// the bulk, so the long cells start before the bulk has ended. Launched
+// cooperatively (all blocks resident), because these warps wait for records
+// that other blocks write.
+struct FuseArgs {
+  uint32_t *claim;       // records claimed by warp-form workers
+  uint32_t *bulk_done;   // bulk warps whose queue loop has ended
+  uint32_t n_bulk_warps;
+};
+
+// Polls without progress after which a waiting warp leaves (its record, and any
+// record left, is then integrated by k_burn_straggler after the launch).
+constexpr uint32_t FUSE_SPIN_LIMIT = 1u << 21;
+
+// Lane 0 waits for record j: 1 once it is written; 0 once every bulk warp is
+// done and record j will never be written; -1 after FUSE_SPIN_LIMIT polls in a
+// row during which neither the cell queue nor the bulk-done count moved. Polls
+// are relaxed loads with a sleep that doubles up to 8 us.
+__device__ __forceinline__ int fuse_wait(const StragArgs &sa, const FuseArgs &fa, uint32_t j,
+                                         const unsigned long long *next) {
+  int r = -1;
+  if (wlane() == 0) {
+    unsigned long long q0 = ld_relaxed(next);
+    uint32_t d0 = ld_relaxed(fa.bulk_done);
+    unsigned ns = 256;
+    for (uint32_t spins = 0; spins < FUSE_SPIN_LIMIT;) {
+      if (ld_relaxed(&sa.flag[j]) != 0u) { r = 1; break; }
+      const uint32_t d = ld_relaxed(fa.bulk_done);
+      // all bulk warps done: the record count is final; a record below it is
+      // written already and its flag shows on a later poll
+      if (d >= fa.n_bulk_warps && j >= min(ld_relaxed(sa.count), sa.cap)) { r = 0; break; }
+      const unsigned long long q = ld_relaxed(next);
+      if (q != q0 || d != d0) {
+        q0 = q;
+        d0 = d;
+        spins = 0;
+      } else {
+        ++spins;
+      }
+      __nanosleep(ns);
+      if (ns < 8192) ns *= 2;
+    }
+  }
+  return __shfl_sync(WFULL, r, 0);
+}
+
+template <int N, typename LT>
+__device__ __forceinline__ void fused_records(const DNet &net, const Opts &o, const CellArgs &a,
+                                              const StragArgs &sa, const FuseArgs &fa,
+                                              const unsigned long long *next, const WSh<LT> &sh) {
+  const Lane<N, LT> *rec = static_cast<const Lane<N, LT> *>(sa.rec);
+  for (;;) {
+    uint32_t j = 0;
+    if (wlane() == 0) j = atomicAdd(fa.claim, 1u);
+    j = __shfl_sync(WFULL, j, 0);
+    if (j >= sa.cap) return;
+    if (fuse_wait(sa, fa, j, next) != 1) return;
+    // every lane observes the flag, then fences: it synchronises with the
+    // release store of the record's writer before reading the record
+    (void)ld_relaxed(&sa.flag[j]);
+    __threadfence();
+    WState<N> W;
+    w_load<N, LT>(W, rec[j], sh, net);
+    while (W.phase != PH_DONE) {
+      const bool ok = w_rhs<N, LT>(W, sh, net);
+      w_advance<N, LT>(W, sh, net, o, ok);
+    }
+    w_store<N>(W, net, a);
+    __syncwarp();
+    if (wlane() == 0) st_release(&sa.flag[j], 2u);
+  }
+}
+
+template <int N, typename LT>
+__global__ void __launch_bounds__(128, 3) k_burn_fused(DNet net, Opts o, CellArgs a, unsigned long long *next,
+                                                       StragArgs sa, FuseArgs fa, int smem_per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  persistent_worker<N, LT>(net, o, a, next, sa);
+  __syncwarp();
+  if (wlane() == 0) {
+    __threadfence();
+    atomicAdd(fa.bulk_done, 1u);
+  }
+  const WSh<LT> sh = wsh_carve<N, LT>(smem + (threadIdx.x >> 5) * (size_t)smem_per_warp, net.R);
+  fused_records<N, LT>(net, o, a, sa, fa, next, sh);
 }
 
 }  // namespace mc

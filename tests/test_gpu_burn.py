@@ -197,6 +197,22 @@ def test_straggler_handoff_parity(mc, make, n, lu):
     assert rep["pass"], rep
 
 
+def test_fused_launch_matches_two_launches(mc):
+    """Bulk and hand-off in one cooperative launch (128-thread blocks) against
+    the bulk launch followed by the straggler launch (64-thread blocks): with
+    every qualifying cell fitting the record list, each cell's arithmetic is
+    the same, so the results agree bit for bit (no record lost or repeated)."""
+    net = network_13()
+    cells = synthetic_cells(net, 16384, seed=3)
+    a = _run(mc, net, cells, 1e10, lu_precision=32, variant=2, straggler_steps=1024, block_threads=128)
+    b = _run(mc, net, cells, 1e10, lu_precision=32, variant=2, straggler_steps=1024, block_threads=64)
+    att = a[3][0] + a[3][1] + a[3][2]
+    print("handed off:", np.mean(att > 1024))
+    assert 0.01 < np.mean(att > 1024) < 0.125
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
 def _segments(mc, batch):
     import torch
     segs, keep = [], []
