@@ -39,6 +39,30 @@ CELL_SEED = 3
 EXP_OPS, LOG_OPS, DIV_OPS = 20, 36, 8
 
 
+# ---- multi-rank bookkeeping (one process per GPU; the cells shard with no
+# exchange, so the only collectives are a barrier and a max of the timings)
+def shard_seed(rank: int) -> int:
+    """Cell seed of a rank's shard: every rank burns its own, independent cells."""
+    return CELL_SEED + 1000 * rank
+
+
+def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
+    """Largest x over all ranks: the slowest rank sets the job's time. Needs an
+    initialised process group when world > 1 (NCCL wants device="cuda")."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job cells/s: the cells of every rank over the slowest rank's time."""
+    return cells_per_rank * world / (ms / 1e3)
+
+
 def fp64_ops_per_cell(S, R, n, stats):
     """FP64 operations of the work the per-cell counters record."""
     rhs, jac, lu, newton, steps = (stats[3].astype(np.float64), stats[4].astype(np.float64),
@@ -229,7 +253,7 @@ def main():
     net = network_13()
     h = mc.Network(net)
     n = args.cells
-    cells = synthetic_cells(net, n, seed=CELL_SEED + 1000 * rank)  # independent shard per rank
+    cells = synthetic_cells(net, n, seed=shard_seed(rank))
     d = to_device(cells)
     x0, T0 = d["x"].clone(), d["T"].clone()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -269,11 +293,7 @@ def main():
         launches = mc.mc_launch_count()
         clocks = clock_sampler_stop(proc, fh, os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv"),
                                     local) if sample_clocks else None
-        ms = total / steps
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(total / steps, world, "cuda")
         return ms, per, launches, clocks
 
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
@@ -283,14 +303,14 @@ def main():
     status = d["status"].cpu().numpy()
     stats = d["stats"].cpu().numpy()
     ops = float(fp64_ops_per_cell(net.n_species, net.n_reactions, net.n_ode, stats).sum())
-    value = n * world / (ms32 / 1e3)
+    value = job_throughput(n, world, ms32)
 
     plain = None
     if not args.no_plain:
         ms64, _, _, _ = timed(opts64, 1, 1)
         st64 = d["stats"].cpu().numpy()
         ops64 = float(fp64_ops_per_cell(net.n_species, net.n_reactions, net.n_ode, st64).sum())
-        plain = {"value": n * world / (ms64 / 1e3), "unit": "cells/s", "ms_per_step": ms64,
+        plain = {"value": job_throughput(n, world, ms64), "unit": "cells/s", "ms_per_step": ms64,
                  "fp64_tflops_algorithmic": 2 * ops64 / (ms64 / 1e3) / 1e12,
                  "ok_fraction": float(np.mean(d["status"].cpu().numpy() == 0))}
 
@@ -310,7 +330,7 @@ def main():
         t1 = time.perf_counter()
         if i > 0:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_v = n * world / (float(np.mean(e2e_ms)) / 1e3)
+    e2e_v = job_throughput(n, world, max_over_ranks(float(np.mean(e2e_ms)), world, "cuda"))
     h2d = (net.n_species + 2) * 8 * n
     d2h = (net.n_species + 1) * 8 * n + 4 * n
 
