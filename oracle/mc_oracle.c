@@ -30,11 +30,18 @@
  * limit, the order of convergence, the step-size rule's target error, the
  * Jacobian against finite differences, and the LU against the definition.
  *
+ * Failure retry (same paragraph 3: retry a zone with different tolerances or
+ * Jacobian approximations): a forward-difference Jacobian (pinned exact on a
+ * linear chain up to rounding, to its closed-form error on Robertson, to the
+ * analytic Jacobian, and through Robertson's published values) and a per-cell
+ * retry ladder (pinned against the plain burn of each rung).
+ *
  * Parity unpinned: the step-control policy constants (when h and q may change,
  * the Jacobian/matrix reuse ages, the failure ladders). They are heuristics
  * with no closed form; they are checked only through solution accuracy and
  * through parity with the independent CUDA implementation of the same rules.
  */
+#include <float.h>
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -88,6 +95,7 @@ typedef struct {
 typedef struct {
     double rtol, atol;
     int max_order, max_steps;
+    int jac_fd;        /* 1: forward-difference Jacobian instead of the analytic one */
 } or_opts;
 
 static double harmonic(int k)
@@ -894,6 +902,53 @@ int or_net_eval(const or_net *net, double ndens, double T_iso, const double *ks,
     return 0;
 }
 
+/* Forward-difference Jacobian: one of the "Jacobian approximations" the     */
+/* paper's failure policy may retry with (Software design section, ¶3). The  */
+/* paper gives no formula; this is the plain one-sided difference           */
+/*   J[:, j] = (f(y + d_j e_j) - f(y)) / d_j,                                 */
+/*   d_j = sqrt(eps) (|y_j| + atol / rtol),                                   */
+/* the increment scaled like the error weight rtol |y_j| + atol, and d_j      */
+/* taken as the difference actually represented, (y_j + d_j) - y_j.          */
+typedef struct {
+    const or_ode *inner;
+    double rtol, atol;
+} or_fd;
+
+static int fd_rhs(void *ctx, double t, const double *y, double *f)
+{
+    const or_fd *p = (const or_fd *)ctx;
+    return p->inner->rhs(p->inner->ctx, t, y, f);
+}
+
+static int fd_jac(void *ctx, double t, const double *y, double *J)
+{
+    const or_fd *p = (const or_fd *)ctx;
+    const or_ode *in = p->inner;
+    const int n = in->n;
+    double f0[OR_NMAX], f1[OR_NMAX], yp[OR_NMAX];
+    if (in->rhs(in->ctx, t, y, f0) != 0) return 1;
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < n; ++i) yp[i] = y[i];
+        yp[j] = y[j] + sqrt(DBL_EPSILON) * (fabs(y[j]) + p->atol / p->rtol);
+        const double dj = yp[j] - y[j];
+        if (!(dj != 0.0)) return 1;
+        if (in->rhs(in->ctx, t, yp, f1) != 0) return 1;
+        for (int i = 0; i < n; ++i) J[i * n + j] = (f1[i] - f0[i]) / dj;
+    }
+    return 0;
+}
+
+/* The forward-difference Jacobian of a network's ODE system at y (for the   */
+/* pins; the integrator uses the same function).                             */
+int or_net_fd_jac(const or_net *net, double ndens, double T_iso, const double *ks, const double *y,
+                  double rtol, double atol, double *J)
+{
+    or_cell c = {net, ndens, T_iso, ks};
+    or_ode ode = {net->S + net->energy, or_net_rhs, or_net_jac, &c};
+    or_fd fd = {&ode, rtol, atol};
+    return fd_jac(&fd, 0.0, y, J);
+}
+
 /* Burn one cell: the operator-split reaction step of length dt (Software
    design section, paragraph 4) for the state (x, T). For the energy form the
    thermal energy u = sum x k_B T/(gamma-1) is integrated and T recovered by
@@ -904,7 +959,10 @@ int or_burn_cell(const or_net *net, const or_opts *o, double dt, double *x, doub
     const int S = net->S;
     double y[OR_NMAX];
     or_cell c = {net, ndens, T ? *T : 1.0, ks};
-    or_ode ode = {S + net->energy, or_net_rhs, or_net_jac, &c};
+    or_ode exact = {S + net->energy, or_net_rhs, or_net_jac, &c};
+    or_fd fd = {&exact, o->rtol, o->atol};
+    or_ode approx = {S + net->energy, fd_rhs, fd_jac, &fd};
+    const or_ode ode = o->jac_fd ? approx : exact;
     for (int i = 0; i < S; ++i) y[i] = x[i];
     if (net->energy) {
         double X = 0.0;
@@ -986,6 +1044,89 @@ int or_burn_batch(const or_net *net, double rtol, double atol, int max_order, in
     for (int i = 1; i < nthreads; ++i)
         if (pthread_create(&th[started], NULL, batch_worker, &b) == 0) started++;
     batch_worker(&b);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Retry ladder (Software design section, ¶3: a zone whose integration fails */
+/* may be retried on its own with different tolerances or Jacobian           */
+/* approximations, or the failure handed back). Each cell is burned from its */
+/* inputs with rung 0; while it fails with a status a retry can change       */
+/* (step cap, step-size underflow, Newton failures, non-finite state) and    */
+/* rungs remain, it is burned again from the same inputs with the next rung. */
+/* The outputs are those of the last attempt, rung[c] says which rung gave   */
+/* them. Rejected inputs are never retried.                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const or_net *net;
+    int n_rungs;
+    const or_opts *rungs;
+    int64_t ncells, ld;
+    double dt;
+    double *x, *T;
+    const double *ndens, *ks;
+    int32_t *status, *stats, *rung;
+    int64_t next;
+} or_ladder;
+
+static void *ladder_worker(void *arg)
+{
+    or_ladder *b = (or_ladder *)arg;
+    const int S = b->net->S, R = b->net->R;
+    for (;;) {
+        int64_t c = __atomic_fetch_add(&b->next, 1, __ATOMIC_RELAXED);
+        if (c >= b->ncells) break;
+        double x0[OR_NMAX], ks[OR_RMAX], x[OR_NMAX], T = 1.0;
+        const double T0 = b->T ? b->T[c] : 1.0;
+        int32_t st[OR_NSTAT];
+        for (int i = 0; i < S; ++i) x0[i] = b->x[i * b->ld + c];
+        if (b->ks)
+            for (int r = 0; r < R; ++r) ks[r] = b->ks[r * b->ld + c];
+        const double nd = b->ndens ? b->ndens[c] : 1.0;
+        int s = OR_BAD_INPUT, k = 0;
+        for (k = 0; k < b->n_rungs; ++k) {
+            for (int i = 0; i < S; ++i) x[i] = x0[i];
+            T = T0;
+            s = or_burn_cell(b->net, &b->rungs[k], b->dt, x, b->T ? &T : NULL, nd, b->ks ? ks : NULL, st);
+            const int retry = (s == OR_MAX_STEPS || s == OR_H_UNDERFLOW || s == OR_CONV_FAIL ||
+                               s == OR_NONFINITE);
+            if (!retry || k + 1 == b->n_rungs) break;
+        }
+        if (s != OR_BAD_INPUT) {
+            for (int i = 0; i < S; ++i) b->x[i * b->ld + c] = x[i];
+            if (b->T) b->T[c] = T;
+        }
+        b->status[c] = s;
+        b->rung[c] = k;
+        if (b->stats)
+            for (int q = 0; q < OR_NSTAT; ++q) b->stats[q * b->ld + c] = st[q];
+    }
+    return NULL;
+}
+
+int or_burn_batch_ladder(const or_net *net, int n_rungs, const double *rtol, const double *atol,
+                         const int32_t *max_order, const int32_t *max_steps, const int32_t *jac_fd,
+                         int64_t ncells, double dt, double *x, int64_t ld, double *T, const double *ndens,
+                         const double *ks, int32_t *status, int32_t *stats, int32_t *rung, int nthreads)
+{
+    if (!net || n_rungs < 1 || n_rungs > 8 || ncells < 0 || ld < ncells || (net->energy && !T) || !rung)
+        return 1;
+    or_opts rungs[8];
+    for (int k = 0; k < n_rungs; ++k) {
+        if (!(rtol[k] > 0.0) || !(atol[k] > 0.0) || max_order[k] < 1 || max_order[k] > OR_QMAX ||
+            max_steps[k] < 1)
+            return 1;
+        rungs[k] = (or_opts){rtol[k], atol[k], max_order[k], max_steps[k], jac_fd[k] ? 1 : 0};
+    }
+    or_ladder b = {net, n_rungs, rungs, ncells, ld, dt, x, T, ndens, ks, status, stats, rung, 0};
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int i = 1; i < nthreads; ++i)
+        if (pthread_create(&th[started], NULL, ladder_worker, &b) == 0) started++;
+    ladder_worker(&b);
     for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
     return 0;
 }

@@ -62,6 +62,11 @@ def lib():
             L.or_burn_batch.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
                                         C.c_int64, C.c_double, _dp, C.c_int64, _dp, _dp, _dp,
                                         _ip, _ip, C.c_int]
+            L.or_net_fd_jac.argtypes = [C.c_void_p, C.c_double, C.c_double, _dp, _dp, C.c_double, C.c_double,
+                                        _dp]
+            L.or_burn_batch_ladder.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _ip, _ip, _ip, C.c_int64,
+                                               C.c_double, _dp, C.c_int64, _dp, _dp, _dp, _ip, _ip, _ip,
+                                               C.c_int]
             L.or_linear_integrate.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_double,
                                               C.c_int, C.c_int, C.c_double, C.c_double, _dp, _ip]
             L.or_linear_fixed_steps.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int, _dp,
@@ -129,6 +134,18 @@ class OracleNetwork:
             raise ValueError("state cannot be evaluated (T <= 0)")
         return (f, J) if jac else f
 
+    def fd_jac(self, y, ndens=1.0, T_iso=1.0, rate_scale=None, rtol=1e-6, atol=1e-10):
+        """Forward-difference Jacobian of one state y (the integrator's
+        alternative to the analytic one)."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        J = np.zeros((y.size, y.size))
+        ks = None if rate_scale is None else np.ascontiguousarray(rate_scale, dtype=np.float64)
+        rc = lib().or_net_fd_jac(self.h, float(ndens), float(T_iso), _d(ks) if ks is not None else None,
+                                 _d(y), float(rtol), float(atol), _d(J))
+        if rc != 0:
+            raise ValueError("state cannot be evaluated")
+        return J
+
 
 def burn(onet: OracleNetwork, cells: dict, dt: float, rtol=1e-6, atol=1e-10, max_order=5,
          max_steps=100000, nthreads=None, index=None):
@@ -152,6 +169,38 @@ def burn(onet: OracleNetwork, cells: dict, dt: float, rtol=1e-6, atol=1e-10, max
     if rc != 0:
         raise ValueError("oracle batch rejected its arguments")
     return x, T, status, stats
+
+
+def burn_ladder(onet: OracleNetwork, cells: dict, dt: float, rungs, nthreads=None, index=None):
+    """Burn cells with a retry ladder: ``rungs`` is a list (1 to 8) of dicts
+    with keys rtol, atol, max_order, max_steps and jac ("analytic" or "fd").
+    A cell that fails with a retryable status is burned again from its inputs
+    with the next rung. Returns (x, T, status, stats, rung), where rung [n]
+    is the rung whose attempt gave the cell's outputs."""
+    net = onet.net
+    sel = (lambda a: a[..., index]) if index is not None else (lambda a: a)
+    x = np.array(sel(np.asarray(cells["x"], dtype=np.float64)), dtype=np.float64, order="C", copy=True)
+    n = x.shape[1]
+    T = None if cells.get("T") is None else np.array(sel(np.asarray(cells["T"], dtype=np.float64)), order="C", copy=True)
+    nd = None if cells.get("ndens") is None else np.ascontiguousarray(sel(np.asarray(cells["ndens"], dtype=np.float64)))
+    ks = None if cells.get("rate_scale") is None else np.ascontiguousarray(sel(np.asarray(cells["rate_scale"], dtype=np.float64)))
+    k = len(rungs)
+    rt = np.array([r.get("rtol", 1e-6) for r in rungs], dtype=np.float64)
+    at = np.array([r.get("atol", 1e-10) for r in rungs], dtype=np.float64)
+    mo = np.array([r.get("max_order", 5) for r in rungs], dtype=np.int32)
+    ms = np.array([r.get("max_steps", 100000) for r in rungs], dtype=np.int32)
+    fd = np.array([1 if r.get("jac", "analytic") == "fd" else 0 for r in rungs], dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    stats = np.zeros((NSTAT, n), dtype=np.int32)
+    rung = np.zeros(n, dtype=np.int32)
+    nthreads = nthreads or os.cpu_count() or 1
+    rc = lib().or_burn_batch_ladder(onet.h, k, _d(rt), _d(at), _i(mo), _i(ms), _i(fd), n, dt, _d(x), n,
+                                    _d(T) if T is not None else None, _d(nd) if nd is not None else None,
+                                    _d(ks) if ks is not None else None, _i(status), _i(stats), _i(rung),
+                                    int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle ladder rejected its arguments")
+    return x, T, status, stats, rung
 
 
 def linear_integrate(A, c, y0, t0, t1, rtol=1e-6, atol=1e-10, max_order=5, max_steps=100000):
