@@ -36,6 +36,10 @@
  * analytic Jacobian, and through Robertson's published values) and a per-cell
  * retry ladder (pinned against the plain burn of each rung).
  *
+ * Coupling by spectral deferred corrections (paragraph 4): an optional
+ * constant source per cell and component added to the right-hand side
+ * (pinned to straight lines, to a matrix exponential, to element totals).
+ *
  * Parity unpinned: the step-control policy constants (when h and q may change,
  * the Jacobian/matrix reuse ages, the failure ladders). They are heuristics
  * with no closed form; they are checked only through solution accuracy and
@@ -742,6 +746,7 @@ typedef struct {
     double ndens;      /* total density n, cm^-3 (1 for dimensionless systems) */
     double T_iso;      /* temperature of an isothermal network */
     const double *ks;  /* per-reaction factors s_r, NULL for all ones */
+    const double *src; /* constant source per ODE component, NULL for none */
 } or_cell;
 
 or_net *or_net_create(int S, int E, int R, int energy, const int32_t *react,
@@ -828,6 +833,10 @@ int or_net_rhs(void *ctx, double t, const double *y, double *f)
         }
         if (net->energy) f[S] += net->dE[r] * wr;
     }
+    /* a constant source (e.g. the advective term of an SDC-coupled burn,    */
+    /* Software design section, paragraph 4) adds to every component         */
+    if (c->src)
+        for (int i = 0; i < S + net->energy; ++i) f[i] += c->src[i];
     return 0;
 }
 
@@ -954,11 +963,11 @@ int or_net_fd_jac(const or_net *net, double ndens, double T_iso, const double *k
    thermal energy u = sum x k_B T/(gamma-1) is integrated and T recovered by
    the EOS inversion at the end. x has S entries; T is in/out. */
 int or_burn_cell(const or_net *net, const or_opts *o, double dt, double *x, double *T,
-                 double ndens, const double *ks, int32_t *st)
+                 double ndens, const double *ks, const double *src, int32_t *st)
 {
     const int S = net->S;
     double y[OR_NMAX];
-    or_cell c = {net, ndens, T ? *T : 1.0, ks};
+    or_cell c = {net, ndens, T ? *T : 1.0, ks, src};
     or_ode exact = {S + net->energy, or_net_rhs, or_net_jac, &c};
     or_fd fd = {&exact, o->rtol, o->atol};
     or_ode approx = {S + net->energy, fd_rhs, fd_jac, &fd};
@@ -1000,6 +1009,7 @@ typedef struct {
     const double *ndens, *ks;
     int32_t *status, *stats;
     int64_t next;
+    const double *src;  /* [n_ode][ld] constant sources, or NULL */
 } or_batch;
 
 static void *batch_worker(void *arg)
@@ -1011,14 +1021,16 @@ static void *batch_worker(void *arg)
         if (c0 >= b->ncells) break;
         int64_t c1 = c0 + 16 < b->ncells ? c0 + 16 : b->ncells;
         for (int64_t c = c0; c < c1; ++c) {
-            double x[OR_NMAX], ks[OR_RMAX], T = b->T ? b->T[c] : 1.0;
+            double x[OR_NMAX], ks[OR_RMAX], src[OR_NMAX], T = b->T ? b->T[c] : 1.0;
             int32_t st[OR_NSTAT];
             for (int i = 0; i < S; ++i) x[i] = b->x[i * b->ld + c];
             if (b->ks)
                 for (int r = 0; r < R; ++r) ks[r] = b->ks[r * b->ld + c];
+            if (b->src)
+                for (int i = 0; i < S + b->net->energy; ++i) src[i] = b->src[i * b->ld + c];
             double nd = b->ndens ? b->ndens[c] : 1.0;
             int s = or_burn_cell(b->net, &b->o, b->dt, x, b->T ? &T : NULL, nd,
-                                 b->ks ? ks : NULL, st);
+                                 b->ks ? ks : NULL, b->src ? src : NULL, st);
             for (int i = 0; i < S; ++i) b->x[i * b->ld + c] = x[i];
             if (b->T) b->T[c] = T;
             b->status[c] = s;
@@ -1029,14 +1041,16 @@ static void *batch_worker(void *arg)
     return NULL;
 }
 
-int or_burn_batch(const or_net *net, double rtol, double atol, int max_order, int max_steps,
-                  int64_t ncells, double dt, double *x, int64_t ld, double *T,
-                  const double *ndens, const double *ks, int32_t *status, int32_t *stats,
-                  int nthreads)
+/* Burn with a constant source per cell and ODE component, src[i * ld + c]   */
+/* (species rates in fraction/s, then the energy rate in eV/s per unit n).   */
+int or_burn_batch_src(const or_net *net, double rtol, double atol, int max_order, int max_steps,
+                      int64_t ncells, double dt, double *x, int64_t ld, double *T,
+                      const double *ndens, const double *ks, const double *src, int32_t *status,
+                      int32_t *stats, int nthreads)
 {
     if (!net || ncells < 0 || ld < ncells || (net->energy && !T)) return 1;
     or_batch b = {net, {rtol, atol, max_order, max_steps}, ncells, ld, dt, x, T, ndens, ks,
-                  status, stats, 0};
+                  status, stats, 0, src};
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     pthread_t th[256];
@@ -1088,7 +1102,8 @@ static void *ladder_worker(void *arg)
         for (k = 0; k < b->n_rungs; ++k) {
             for (int i = 0; i < S; ++i) x[i] = x0[i];
             T = T0;
-            s = or_burn_cell(b->net, &b->rungs[k], b->dt, x, b->T ? &T : NULL, nd, b->ks ? ks : NULL, st);
+            s = or_burn_cell(b->net, &b->rungs[k], b->dt, x, b->T ? &T : NULL, nd, b->ks ? ks : NULL, NULL,
+                             st);
             const int retry = (s == OR_MAX_STEPS || s == OR_H_UNDERFLOW || s == OR_CONV_FAIL ||
                                s == OR_NONFINITE);
             if (!retry || k + 1 == b->n_rungs) break;
@@ -1129,6 +1144,15 @@ int or_burn_batch_ladder(const or_net *net, int n_rungs, const double *rtol, con
     ladder_worker(&b);
     for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
     return 0;
+}
+
+int or_burn_batch(const or_net *net, double rtol, double atol, int max_order, int max_steps,
+                  int64_t ncells, double dt, double *x, int64_t ld, double *T,
+                  const double *ndens, const double *ks, int32_t *status, int32_t *stats,
+                  int nthreads)
+{
+    return or_burn_batch_src(net, rtol, atol, max_order, max_steps, ncells, dt, x, ld, T, ndens, ks,
+                             NULL, status, stats, nthreads);
 }
 
 int or_nstat(void) { return OR_NSTAT; }

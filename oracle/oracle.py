@@ -62,6 +62,9 @@ def lib():
             L.or_burn_batch.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
                                         C.c_int64, C.c_double, _dp, C.c_int64, _dp, _dp, _dp,
                                         _ip, _ip, C.c_int]
+            L.or_burn_batch_src.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
+                                            C.c_int64, C.c_double, _dp, C.c_int64, _dp, _dp, _dp, _dp,
+                                            _ip, _ip, C.c_int]
             L.or_net_fd_jac.argtypes = [C.c_void_p, C.c_double, C.c_double, _dp, _dp, C.c_double, C.c_double,
                                         _dp]
             L.or_burn_batch_ladder.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _ip, _ip, _ip, C.c_int64,
@@ -148,10 +151,12 @@ class OracleNetwork:
 
 
 def burn(onet: OracleNetwork, cells: dict, dt: float, rtol=1e-6, atol=1e-10, max_order=5,
-         max_steps=100000, nthreads=None, index=None):
+         max_steps=100000, nthreads=None, index=None, source=None):
     """Burn cells (SoA dict from mc_inputs) on host threads. ``index`` selects
-    a subset of the cells. Returns (x [S, n], T [n] or None, status [n],
-    stats [NSTAT, n])."""
+    a subset of the cells. ``source`` [n_ode, n] is a constant source added to
+    each cell's right-hand side (species rates, then the energy rate), as in a
+    burn coupled by spectral deferred corrections. Returns (x [S, n], T [n] or
+    None, status [n], stats [NSTAT, n])."""
     net = onet.net
     x = np.asarray(cells["x"], dtype=np.float64)
     sel = (lambda a: a[..., index]) if index is not None else (lambda a: a)
@@ -163,9 +168,18 @@ def burn(onet: OracleNetwork, cells: dict, dt: float, rtol=1e-6, atol=1e-10, max
     status = np.zeros(n, dtype=np.int32)
     stats = np.zeros((NSTAT, n), dtype=np.int32)
     nthreads = nthreads or os.cpu_count() or 1
-    rc = lib().or_burn_batch(onet.h, rtol, atol, max_order, max_steps, n, dt, _d(x), n,
-                             _d(T) if T is not None else None, _d(nd) if nd is not None else None,
-                             _d(ks) if ks is not None else None, _i(status), _i(stats), int(nthreads))
+    if source is None:
+        rc = lib().or_burn_batch(onet.h, rtol, atol, max_order, max_steps, n, dt, _d(x), n,
+                                 _d(T) if T is not None else None, _d(nd) if nd is not None else None,
+                                 _d(ks) if ks is not None else None, _i(status), _i(stats), int(nthreads))
+    else:
+        src = np.array(sel(np.asarray(source, dtype=np.float64)), dtype=np.float64, order="C", copy=True)
+        if src.shape != (net.n_ode, n):
+            raise ValueError(f"source must be [{net.n_ode}, {n}]")
+        rc = lib().or_burn_batch_src(onet.h, rtol, atol, max_order, max_steps, n, dt, _d(x), n,
+                                     _d(T) if T is not None else None, _d(nd) if nd is not None else None,
+                                     _d(ks) if ks is not None else None, _d(src), _i(status), _i(stats),
+                                     int(nthreads))
     if rc != 0:
         raise ValueError("oracle batch rejected its arguments")
     return x, T, status, stats
