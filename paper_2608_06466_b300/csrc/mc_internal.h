@@ -59,6 +59,18 @@ struct Tuned {
 };
 Tuned autotune_pick(const mc_network *net, const mc_burn_opts &o);
 
+// Kernel attributes belong to a device. Per device, the largest value this
+// thread has already raised an attribute to, so each (thread, device) sets it
+// once and a second device on the same thread is not skipped.
+struct DevAttrCache {
+  static constexpr int kDevices = 64;
+  int value[kDevices] = {};
+  bool below(int dev, int v) const { return dev < 0 || dev >= kDevices || value[dev] < v; }
+  void raise(int dev, int v) {
+    if (dev >= 0 && dev < kDevices && value[dev] < v) value[dev] = v;
+  }
+};
+
 // Launch the burn kernel of ODE-count bucket N (network n <= N) with matrix
 // precision LT; defined in mc_launch.cuh, instantiated in mc_inst_<N>.cu.
 template <int N, typename LT>

@@ -23,11 +23,11 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
     const int per_warp = (int)wsh_bytes<N, LT>(d.R);
     const int wthreads = 128;
     const int smem = per_warp * (wthreads / 32);
-    static thread_local int configured_w = 0;
-    if (configured_w < smem) {
+    static thread_local DevAttrCache configured_w;
+    if (configured_w.below(dev, smem)) {
       e = cudaFuncSetAttribute(k_burn_warp<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return cuda_error(e, "warp kernel smem attribute");
-      configured_w = smem;
+      configured_w.raise(dev, smem);
     }
     int64_t blocks = (int64_t)sms * std::max(1, blocks_per_sm) * 2;
     const int64_t need = a.n_dev ? blocks : (a.n_cells + 3) / 4;
@@ -70,19 +70,23 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
         // one cooperative launch (every block resident): warps whose queue is
         // drained integrate the records while the rest of the bulk still runs
         const int fsmem = per_warp * 4;
-        static thread_local int configured_f = 0;
+        const int fsmem_sm = fsmem * std::max(1, blocks_per_sm);
+        static thread_local DevAttrCache configured_f, carveout_f;
         e = cudaSuccess;
-        if (configured_f < fsmem) {
+        if (configured_f.below(dev, fsmem) || carveout_f.below(dev, fsmem_sm)) {
           e = cudaFuncSetAttribute(k_burn_fused<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsmem);
           // shared-memory carveout just large enough for the resident blocks: the
           // rest stays L1, which caches the thread-form lanes' spilled state
           int smem_sm = 0;
           if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
           if (e == cudaSuccess && smem_sm > 0) {
-            const int pct = std::min(100, (int)((100LL * fsmem * blocks_per_sm + smem_sm - 1) / smem_sm) + 1);
+            const int pct = std::min(100, (int)((100LL * fsmem_sm + smem_sm - 1) / smem_sm) + 1);
             e = cudaFuncSetAttribute(k_burn_fused<N, LT>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
           }
-          if (e == cudaSuccess) configured_f = fsmem;
+          if (e == cudaSuccess) {
+            configured_f.raise(dev, fsmem);
+            carveout_f.raise(dev, fsmem_sm);
+          }
         }
         int per_sm = 0;
         if (e == cudaSuccess)
@@ -112,11 +116,11 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
       // step logic
       const int wthreads = 32;
       const int smem = per_warp;
-      static thread_local int configured = 0;
-      if (configured < smem) {
+      static thread_local DevAttrCache configured;
+      if (configured.below(dev, smem)) {
         e = cudaFuncSetAttribute(k_burn_straggler<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return cuda_error(e, "straggler smem attribute");
-        configured = smem;
+        configured.raise(dev, smem);
       }
       e = cudaMemsetAsync(next + 1, 0, sizeof(unsigned long long), st);
       if (e != cudaSuccess) return cuda_error(e, "straggler queue reset");

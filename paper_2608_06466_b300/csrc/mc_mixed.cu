@@ -100,13 +100,13 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
   const int msmem = (int)per_warp * (mthreads / 32);
   {
     // both precisions run in one call (FP32 pass, FP64 retry pass)
-    static thread_local int configured = 0;
-    if (configured < msmem) {
+    static thread_local DevAttrCache configured;
+    if (configured.below(dev, msmem)) {
       cudaError_t ea = cudaFuncSetAttribute(k_burn_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
       if (ea == cudaSuccess)
         ea = cudaFuncSetAttribute(k_burn_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
       if (ea != cudaSuccess) return cuda_error(ea, "mixed smem attribute");
-      configured = msmem;
+      configured.raise(dev, msmem);
     }
   }
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long) * nseg, st);
