@@ -36,6 +36,10 @@
  * analytic Jacobian, and through Robertson's published values) and a per-cell
  * retry ladder (pinned against the plain burn of each rung).
  *
+ * Alternative integrator (paragraph 4's network/integrator separation): RKC,
+ * explicit Runge-Kutta-Chebyshev of order 2 (pinned to its closed-form
+ * stability polynomial, its order, closed forms and Robertson's values).
+ *
  * Coupling by spectral deferred corrections (paragraph 4): an optional
  * constant source per cell and component added to the right-hand side
  * (pinned to straight lines, to a matrix exponential, to element totals).
@@ -100,6 +104,7 @@ typedef struct {
     double rtol, atol;
     int max_order, max_steps;
     int jac_fd;        /* 1: forward-difference Jacobian instead of the analytic one */
+    int method;        /* 0: BDF (the paper's VODE-style integrator), 1: RKC */
 } or_opts;
 
 static double harmonic(int k)
@@ -401,7 +406,7 @@ static double initial_step(const or_ode *ode, double t0, double span, const doub
     double d0 = wrms(n, y0, w), d1 = wrms(n, f0, w);
     double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
     h0 = fmin(h0, span);
-    double y1[OR_NMAX], f1[OR_NMAX];
+    double y1[OR_NMAX] = {0.0}, f1[OR_NMAX];
     for (int i = 0; i < n; ++i) y1[i] = y0[i] + h0 * f0[i];
     st[ST_RHS] += 1;
     if (ode->rhs(ode->ctx, t0 + h0, y1, f1) != 0 || !all_finite(n, f1)) return h0;
@@ -720,6 +725,203 @@ int or_linear_fixed_steps(int n, const double *A, int deg, const double *c, int 
 }
 
 /* ------------------------------------------------------------------------ */
+/* RKC: the explicit, stabilised Runge-Kutta-Chebyshev method of order 2     */
+/* (Sommeijer, Shampine & Verwer 1998) -- the alternative integrator the     */
+/* network/integrator separation admits (Software design section, ¶4). With  */
+/* s stages and damping eps = 2/13:                                          */
+/*   w0 = 1 + eps/s^2, w1 = T_s'(w0) / T_s''(w0),                             */
+/*   b_j = T_j''(w0) / T_j'(w0)^2 (j >= 2), b_0 = b_1 = b_2,                  */
+/*   Y_0 = y_n, Y_1 = Y_0 + b_1 w1 h F(Y_0),                                  */
+/*   Y_j = (1 - mu_j - nu_j) Y_0 + mu_j Y_{j-1} + nu_j Y_{j-2}                */
+/*         + mt_j h F(Y_{j-1}) + gt_j h F(Y_0),                               */
+/*   mu_j = 2 b_j w0 / b_{j-1}, nu_j = -b_j / b_{j-2}, mt_j = 2 b_j w1 / b_{j-1}, */
+/*   gt_j = -(1 - b_{j-1} T_{j-1}(w0)) mt_j,  y_{n+1} = Y_s.                  */
+/* Stage j sits at time t_n + c_j h, c_j = w1 T_j''(w0) / T_j'(w0) (j >= 2),   */
+/* c_1 = c_2 / T_2'(w0). On y' = lambda y a step multiplies y by             */
+/*   P_s(z) = 1 - b_s T_s(w0) + b_s T_s(w0 + w1 z), z = h lambda,             */
+/* bounded by 1 on [-beta_s, 0], beta_s = (1 + w0) / w1 (about 0.65 s^2).      */
+/* Error estimate of the same paper: (12 (y_n - y_{n+1}) + 6 h (F_n + F_{n+1})) / 15. */
+/* ------------------------------------------------------------------------ */
+#define OR_RKC_EPS (2.0 / 13.0)
+#define OR_RKC_SMAX 256
+
+typedef struct {
+    int s;
+    double w0, w1;
+    double T[OR_RKC_SMAX + 1], dT[OR_RKC_SMAX + 1], ddT[OR_RKC_SMAX + 1], b[OR_RKC_SMAX + 1];
+} or_rkc_coef;
+
+/* Chebyshev values and first two derivatives at w0 by their three-term
+   recurrences, then w1 and the b_j. */
+static void rkc_coef(int s, or_rkc_coef *k)
+{
+    const double w0 = 1.0 + OR_RKC_EPS / ((double)s * s);
+    k->s = s;
+    k->w0 = w0;
+    k->T[0] = 1.0; k->dT[0] = 0.0; k->ddT[0] = 0.0;
+    k->T[1] = w0;  k->dT[1] = 1.0; k->ddT[1] = 0.0;
+    for (int j = 2; j <= s; ++j) {
+        k->T[j] = 2.0 * w0 * k->T[j - 1] - k->T[j - 2];
+        k->dT[j] = 2.0 * k->T[j - 1] + 2.0 * w0 * k->dT[j - 1] - k->dT[j - 2];
+        k->ddT[j] = 4.0 * k->dT[j - 1] + 2.0 * w0 * k->ddT[j - 1] - k->ddT[j - 2];
+    }
+    k->w1 = k->dT[s] / k->ddT[s];
+    for (int j = 2; j <= s; ++j) k->b[j] = k->ddT[j] / (k->dT[j] * k->dT[j]);
+    k->b[0] = k->b[1] = k->b[2];
+}
+
+/* Left end of the real stability interval: w0 + w1 z = -1. */
+static double rkc_beta(int s)
+{
+    or_rkc_coef k;
+    rkc_coef(s, &k);
+    return (1.0 + k.w0) / k.w1;
+}
+
+/* One RKC step of size h from (t, y0) with F(y0) = f0; result in ys. Returns 0,
+   or 1 if a stage's right-hand side cannot be evaluated. */
+static int rkc_step(const or_ode *ode, const or_rkc_coef *k, double t, double h, const double *y0,
+                    const double *f0, double *ys, int32_t *st)
+{
+    const int n = ode->n, s = k->s;
+    double a[OR_NMAX], b[OR_NMAX], F[OR_NMAX];
+    double *ym2 = a, *ym1 = b;
+    const double c2 = k->w1 * k->ddT[2] / k->dT[2];
+    double cprev = c2 / k->dT[2];                       /* c_1 */
+    for (int i = 0; i < n; ++i) {
+        ym2[i] = y0[i];
+        ym1[i] = y0[i] + k->b[1] * k->w1 * h * f0[i];
+    }
+    for (int j = 2; j <= s; ++j) {
+        if (ode->rhs(ode->ctx, t + cprev * h, ym1, F) != 0) return 1;
+        st[ST_RHS] += 1;
+        const double mu = 2.0 * k->b[j] * k->w0 / k->b[j - 1];
+        const double nu = -k->b[j] / k->b[j - 2];
+        const double mt = 2.0 * k->b[j] * k->w1 / k->b[j - 1];
+        const double gt = -(1.0 - k->b[j - 1] * k->T[j - 1]) * mt;
+        for (int i = 0; i < n; ++i) {
+            const double v = (1.0 - mu - nu) * y0[i] + mu * ym1[i] + nu * ym2[i] + mt * h * F[i] +
+                             gt * h * f0[i];
+            ym2[i] = v;                                   /* ym2 now holds Y_j */
+        }
+        double *tmp = ym2; ym2 = ym1; ym1 = tmp;         /* (Y_{j-1}, Y_j) */
+        cprev = k->w1 * k->ddT[j] / k->dT[j];
+    }
+    for (int i = 0; i < n; ++i) ys[i] = ym1[i];
+    return 0;
+}
+
+/* Upper bound on the spectral radius of J: the largest absolute row sum
+   (Gershgorin). */
+static double gershgorin(int n, const double *J)
+{
+    double r = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < n; ++j) a += fabs(J[i * n + j]);
+        if (a > r) r = a;
+    }
+    return r;
+}
+
+/* Adaptive RKC from t0 to t1 (the builder's step control; the paper gives
+   none): each step takes the fewest stages s >= 2 whose interval covers
+   h rho, rho the Gershgorin bound of the Jacobian at the step's start; with
+   more than OR_RKC_SMAX stages needed the step shrinks instead. A step is
+   accepted when the WRMS norm of the estimate, with weights
+   rtol max(|y_n|, |y_{n+1}|) + atol, is at most 1; the next step is
+   h min(10, max(0.1, 0.8 err^(-1/3))), at most h after a rejection. Counters:
+   accepted steps, rejections, right-hand sides, Jacobians (for rho), and the
+   largest stage count in the order slot. */
+int or_rkc_integrate(const or_ode *ode, const or_opts *o, double t0, double t1, double *y, int32_t *st)
+{
+    const int n = ode->n;
+    double f0[OR_NMAX], w[OR_NMAX], yn[OR_NMAX], fn[OR_NMAX], J[OR_NMAX * OR_NMAX], est[OR_NMAX];
+    for (int k = 0; k < OR_NSTAT; ++k) st[k] = 0;
+    if (n < 1 || n > OR_NMAX || !(t1 > t0) || !all_finite(n, y)) return OR_BAD_INPUT;
+    if (ode->rhs(ode->ctx, t0, y, f0) != 0 || !all_finite(n, f0)) return OR_BAD_INPUT;
+    st[ST_RHS] += 1;
+    weights(n, y, o->rtol, o->atol, w);
+    double h = initial_step(ode, t0, t1 - t0, y, f0, w, st);
+    double t = t0;
+    int attempts = 0, rejected = 0;
+    const double beta_max = rkc_beta(OR_RKC_SMAX);
+    while (t < t1) {
+        if (attempts >= o->max_steps) return OR_MAX_STEPS;
+        int last = 0;
+        if (t + h >= t1) { h = t1 - t; last = 1; }
+        if (ode->jac(ode->ctx, t, y, J) != 0 || !all_finite(n * n, J)) return OR_NONFINITE;
+        st[ST_JAC] += 1;
+        const double rho = gershgorin(n, J);
+        if (h * rho > beta_max) { h = 0.95 * beta_max / rho; last = 0; }
+        int s = 2;
+        while (s < OR_RKC_SMAX && rkc_beta(s) < h * rho) ++s;
+        or_rkc_coef k;
+        rkc_coef(s, &k);
+        if (s > st[ST_ORDER]) st[ST_ORDER] = s;
+        attempts += 1;
+        double err = 2.0;
+        int ok = rkc_step(ode, &k, t, h, y, f0, yn, st) == 0 && all_finite(n, yn);
+        if (ok) ok = ode->rhs(ode->ctx, t + h, yn, fn) == 0 && all_finite(n, fn);
+        if (ok) {
+            st[ST_RHS] += 1;
+            for (int i = 0; i < n; ++i) {
+                est[i] = (12.0 * (y[i] - yn[i]) + 6.0 * h * (f0[i] + fn[i])) / 15.0;
+                w[i] = o->rtol * fmax(fabs(y[i]), fabs(yn[i])) + o->atol;
+            }
+            err = wrms(n, est, w);
+        }
+        if (ok && err <= 1.0) {
+            t = last ? t1 : t + h;
+            for (int i = 0; i < n; ++i) { y[i] = yn[i]; f0[i] = fn[i]; }
+            st[ST_STEPS] += 1;
+            double fac = err > 0.0 ? 0.8 * pow(err, -1.0 / 3.0) : 10.0;
+            fac = fmin(10.0, fmax(0.1, fac));
+            if (rejected) fac = fmin(fac, 1.0);
+            rejected = 0;
+            h *= fac;
+        } else {
+            st[ST_ERR_FAILS] += 1;
+            rejected = 1;
+            const double fac = ok ? fmin(1.0, fmax(0.1, 0.8 * pow(err, -1.0 / 3.0))) : 0.25;
+            h *= fac;
+        }
+        if (t < t1 && t + h == t) return OR_H_UNDERFLOW;
+    }
+    return OR_OK;
+}
+
+/* For the pins: one RKC step with s stages on y' = A y + sum_k c_k t^k, and
+   the adaptive RKC on the same system. */
+int or_rkc_linear_step(int n, const double *A, int deg, const double *c, int s, double t, double h,
+                       double *y)
+{
+    or_linear p;
+    or_ode ode;
+    double f0[OR_NMAX], ys[OR_NMAX];
+    int32_t st[OR_NSTAT] = {0};
+    if (n < 1 || n > OR_NMAX || deg < 0 || deg > 7 || s < 2 || s > OR_RKC_SMAX) return 1;
+    linear_ode(&p, n, A, deg, c, &ode);
+    if (ode.rhs(ode.ctx, t, y, f0) != 0) return 1;
+    or_rkc_coef k;
+    rkc_coef(s, &k);
+    if (rkc_step(&ode, &k, t, h, y, f0, ys, st) != 0) return 1;
+    for (int i = 0; i < n; ++i) y[i] = ys[i];
+    return 0;
+}
+
+int or_rkc_linear_integrate(int n, const double *A, int deg, const double *c, double rtol, double atol,
+                            int max_steps, double t0, double t1, double *y, int32_t *st)
+{
+    or_linear p;
+    or_ode ode;
+    if (n < 1 || n > OR_NMAX || deg < 0 || deg > 7) return OR_BAD_INPUT;
+    linear_ode(&p, n, A, deg, c, &ode);
+    or_opts o = {rtol, atol, 2, max_steps, 0, 1};
+    return or_rkc_integrate(&ode, &o, t0, t1, y, st);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Reaction network: rates, right-hand side, Jacobian.                       */
 /*                                                                           */
 /* State y = (x_1..x_S) for an isothermal network, or (x_1..x_S, u) with the  */
@@ -986,7 +1188,8 @@ int or_burn_cell(const or_net *net, const or_opts *o, double dt, double *x, doub
         for (int k = 0; k < OR_NSTAT; ++k) st[k] = 0;
         return OR_BAD_INPUT;
     }
-    int status = or_bdf_integrate(&ode, o, 0.0, dt, y, st);
+    int status = o->method == 1 ? or_rkc_integrate(&ode, o, 0.0, dt, y, st)
+                                : or_bdf_integrate(&ode, o, 0.0, dt, y, st);
     for (int i = 0; i < S; ++i) x[i] = y[i];
     if (net->energy) {
         double X = 0.0;
@@ -1122,7 +1325,7 @@ static void *ladder_worker(void *arg)
 
 int or_burn_batch_ladder(const or_net *net, int n_rungs, const double *rtol, const double *atol,
                          const int32_t *max_order, const int32_t *max_steps, const int32_t *jac_fd,
-                         int64_t ncells, double dt, double *x, int64_t ld, double *T, const double *ndens,
+                         const int32_t *method, int64_t ncells, double dt, double *x, int64_t ld, double *T, const double *ndens,
                          const double *ks, int32_t *status, int32_t *stats, int32_t *rung, int nthreads)
 {
     if (!net || n_rungs < 1 || n_rungs > 8 || ncells < 0 || ld < ncells || (net->energy && !T) || !rung)
@@ -1132,7 +1335,8 @@ int or_burn_batch_ladder(const or_net *net, int n_rungs, const double *rtol, con
         if (!(rtol[k] > 0.0) || !(atol[k] > 0.0) || max_order[k] < 1 || max_order[k] > OR_QMAX ||
             max_steps[k] < 1)
             return 1;
-        rungs[k] = (or_opts){rtol[k], atol[k], max_order[k], max_steps[k], jac_fd[k] ? 1 : 0};
+        if (method[k] != 0 && method[k] != 1) return 1;
+        rungs[k] = (or_opts){rtol[k], atol[k], max_order[k], max_steps[k], jac_fd[k] ? 1 : 0, method[k]};
     }
     or_ladder b = {net, n_rungs, rungs, ncells, ld, dt, x, T, ndens, ks, status, stats, rung, 0};
     if (nthreads < 1) nthreads = 1;

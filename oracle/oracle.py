@@ -67,7 +67,10 @@ def lib():
                                             _ip, _ip, C.c_int]
             L.or_net_fd_jac.argtypes = [C.c_void_p, C.c_double, C.c_double, _dp, _dp, C.c_double, C.c_double,
                                         _dp]
-            L.or_burn_batch_ladder.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _ip, _ip, _ip, C.c_int64,
+            L.or_rkc_linear_step.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_double, C.c_double, _dp]
+            L.or_rkc_linear_integrate.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_double, C.c_int,
+                                                  C.c_double, C.c_double, _dp, _ip]
+            L.or_burn_batch_ladder.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _ip, _ip, _ip, _ip, C.c_int64,
                                                C.c_double, _dp, C.c_int64, _dp, _dp, _dp, _ip, _ip, _ip,
                                                C.c_int]
             L.or_linear_integrate.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_double,
@@ -187,7 +190,8 @@ def burn(onet: OracleNetwork, cells: dict, dt: float, rtol=1e-6, atol=1e-10, max
 
 def burn_ladder(onet: OracleNetwork, cells: dict, dt: float, rungs, nthreads=None, index=None):
     """Burn cells with a retry ladder: ``rungs`` is a list (1 to 8) of dicts
-    with keys rtol, atol, max_order, max_steps and jac ("analytic" or "fd").
+    with keys rtol, atol, max_order, max_steps, jac ("analytic" or "fd") and
+    method ("bdf" or "rkc", the explicit Runge-Kutta-Chebyshev integrator).
     A cell that fails with a retryable status is burned again from its inputs
     with the next rung. Returns (x, T, status, stats, rung), where rung [n]
     is the rung whose attempt gave the cell's outputs."""
@@ -204,17 +208,40 @@ def burn_ladder(onet: OracleNetwork, cells: dict, dt: float, rungs, nthreads=Non
     mo = np.array([r.get("max_order", 5) for r in rungs], dtype=np.int32)
     ms = np.array([r.get("max_steps", 100000) for r in rungs], dtype=np.int32)
     fd = np.array([1 if r.get("jac", "analytic") == "fd" else 0 for r in rungs], dtype=np.int32)
+    meth = np.array([{"bdf": 0, "rkc": 1}[r.get("method", "bdf")] for r in rungs], dtype=np.int32)
     status = np.zeros(n, dtype=np.int32)
     stats = np.zeros((NSTAT, n), dtype=np.int32)
     rung = np.zeros(n, dtype=np.int32)
     nthreads = nthreads or os.cpu_count() or 1
-    rc = lib().or_burn_batch_ladder(onet.h, k, _d(rt), _d(at), _i(mo), _i(ms), _i(fd), n, dt, _d(x), n,
+    rc = lib().or_burn_batch_ladder(onet.h, k, _d(rt), _d(at), _i(mo), _i(ms), _i(fd), _i(meth), n, dt, _d(x), n,
                                     _d(T) if T is not None else None, _d(nd) if nd is not None else None,
                                     _d(ks) if ks is not None else None, _i(status), _i(stats), _i(rung),
                                     int(nthreads))
     if rc != 0:
         raise ValueError("oracle ladder rejected its arguments")
     return x, T, status, stats, rung
+
+
+def rkc_linear_step(A, c, y, t, h, s):
+    """One RKC step with s stages on y' = A y + sum_k c[k] t^k."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    c = np.ascontiguousarray(np.atleast_2d(c), dtype=np.float64)
+    y = np.array(y, dtype=np.float64, copy=True)
+    if lib().or_rkc_linear_step(y.size, _d(A), c.shape[0] - 1, _d(c), int(s), float(t), float(h), _d(y)) != 0:
+        raise ValueError("rkc step rejected its arguments")
+    return y
+
+
+def rkc_linear_integrate(A, c, y0, t0, t1, rtol=1e-6, atol=1e-10, max_steps=100000):
+    """Integrate y' = A y + sum_k c[k] t^k from t0 to t1 with the adaptive RKC.
+    Returns (y, status, stats)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    c = np.ascontiguousarray(np.atleast_2d(c), dtype=np.float64)
+    y = np.array(y0, dtype=np.float64, copy=True)
+    st = np.zeros(NSTAT, dtype=np.int32)
+    s = lib().or_rkc_linear_integrate(y.size, _d(A), c.shape[0] - 1, _d(c), rtol, atol, max_steps, t0, t1,
+                                      _d(y), _i(st))
+    return y, s, st
 
 
 def linear_integrate(A, c, y0, t0, t1, rtol=1e-6, atol=1e-10, max_order=5, max_steps=100000):
