@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmc.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2608_06466_b300.build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2608_06466_b300/build.py` "
                       "(there is no CPU fallback)")
 lib = C.CDLL(LIB_PATH)
 
