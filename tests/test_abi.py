@@ -18,9 +18,8 @@ def _declared():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_2608_06466_b300 import build
-    lib_path = build.build()
-    lib = ctypes.CDLL(lib_path)
+    # built at session start (tests/conftest.py)
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2608_06466_b300", "libmc.so"))
     missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
     assert not missing, f"declared in include/ but not exported: {missing}"
     assert lib.mc_version() >= 1
