@@ -242,6 +242,15 @@ def main():
 
     import torch
     import torch.distributed as dist
+    if not os.path.exists(os.path.join(ROOT, "paper_2608_06466_b300", "libmc.so")):
+        # a fresh checkout: build the library (loading the build script by path,
+        # since importing the package needs the library)
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("_mc_build",
+                                                      os.path.join(ROOT, "paper_2608_06466_b300", "build.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build()
     import paper_2608_06466_b300 as mc
     from paper_2608_06466_b300.api import to_device
     from mc_inputs import network_13, synthetic_cells
