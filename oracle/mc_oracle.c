@@ -27,8 +27,11 @@
  * Robertson values at t = 40, the A->B->C closed form, element and energy
  * conservation, brute-force backward Euler, exactness of the step on
  * polynomials, exactness of the q and q-1 error estimates, the q+1 estimate's
- * limit, the order of convergence, the step-size rule's target error, the
- * Jacobian against finite differences, and the LU against the definition.
+ * limit, the order of convergence, the starting step's closed form on linear
+ * problems, the modified Newton correction (one exact correction on a linear
+ * problem with a current matrix; the contraction factor of the scaled
+ * correction with a matrix formed at another gamma), the Jacobian against
+ * finite differences, and the LU against the definition.
  *
  * Failure retry (same paragraph 3: retry a zone with different tolerances or
  * Jacobian approximations): a forward-difference Jacobian (pinned exact on a
@@ -44,10 +47,12 @@
  * constant source per cell and component added to the right-hand side
  * (pinned to straight lines, to a matrix exponential, to element totals).
  *
- * Parity unpinned: the step-control policy constants (when h and q may change,
- * the Jacobian/matrix reuse ages, the failure ladders). They are heuristics
- * with no closed form; they are checked only through solution accuracy and
- * through parity with the independent CUDA implementation of the same rules.
+ * Parity unpinned: the step-control policy (the step-size factors
+ * eta = 1/((BIAS E)^(1/(k+1)) + ADDON) and their bounds, when h and q may
+ * change, the Newton convergence constants, the Jacobian/matrix reuse ages, the
+ * failure ladders). These are heuristics with no closed form; they are checked
+ * only through solution accuracy and through parity with the independent CUDA
+ * implementation of the same rules.
  */
 #include <float.h>
 #include <math.h>
@@ -327,6 +332,8 @@ typedef struct {
     double J[OR_NMAX * OR_NMAX], P[OR_NMAX * OR_NMAX];
     int piv[OR_NMAX];
     int32_t *st;
+    double *trace;     /* optional: e after each Newton correction (the pins' record) */
+    int ntrace;
 } or_bdf;
 
 enum { NW_CONVERGED = 0, NW_FAIL = 1, NW_FAIL_RHS = 2 };
@@ -386,6 +393,10 @@ static int newton(or_bdf *s, const or_ode *ode, const double *w, const double *l
         for (int i = 0; i < n; ++i) {
             e[i] += d[i];
             y[i] = s->z[i] + e[i];
+        }
+        if (s->trace && s->ntrace < OR_MAXCOR) {
+            for (int i = 0; i < n; ++i) s->trace[s->ntrace * n + i] = e[i];
+            s->ntrace += 1;
         }
         if (m > 0) s->crate = fmax(OR_CRDOWN * s->crate, del / delp);
         double dcon = del * fmin(1.0, s->crate) * cq / OR_CORTES;
@@ -722,6 +733,62 @@ int or_linear_fixed_steps(int n, const double *A, int deg, const double *c, int 
     if (n < 1 || n > OR_NMAX || q < 1 || q > OR_QMAX || deg < 0 || deg > 7) return 1;
     linear_ode(&p, n, A, deg, c, &ode);
     return or_fixed_steps(&ode, q, nsteps, hs, t0, z, hist, e_out, est_out);
+}
+
+/* Starting step of initial_step for y' = A y at y0 (t0 = 0), weights from y0
+   as the integrator takes them. For the pins: its closed form on scalar and
+   diagonal linear problems. */
+double or_linear_initial_step(int n, const double *A, const double *y0, double rtol, double atol,
+                              double span)
+{
+    or_linear p;
+    or_ode ode;
+    double c[OR_NMAX] = {0.0}, f0[OR_NMAX], w[OR_NMAX];
+    int32_t st[OR_NSTAT] = {0};
+    if (n < 1 || n > OR_NMAX) return -1.0;
+    linear_ode(&p, n, A, 0, c, &ode);
+    linear_rhs(&p, 0.0, y0, f0);
+    weights(n, y0, rtol, atol, w);
+    return initial_step(&ode, 0.0, span, y0, f0, w, st);
+}
+
+/* One call of the integrator's modified Newton (newton) on y' = A y for the
+   predicted Nordsieck columns z0 = z[0..n), z1 = z[n..2n) with corrector
+   coefficient l1 and step h, weights w, error constant cq. The matrix is first
+   formed and factored at gamma_P = gamma_p_ratio * h / l1 (by a Newton call at
+   that gamma), then the recorded call runs at gamma = h / l1 and reuses it,
+   scaling its corrections by 2 / (1 + gamma/gamma_P) when the two differ.
+   trace[k n + i] receives e after correction k (at most OR_MAXCOR); returns the
+   number recorded, and *result the newton() outcome (0 converged, 1 failed). */
+int or_linear_newton(int n, const double *A, const double *z, double l1, double h,
+                     double gamma_p_ratio, const double *w, double cq, double *trace, int *result)
+{
+    or_linear p;
+    or_ode ode;
+    double c[OR_NMAX] = {0.0}, l[OR_QMAX + 2] = {1.0, l1}, e[OR_NMAX], y[OR_NMAX];
+    int32_t st[OR_NSTAT] = {0};
+    if (n < 1 || n > OR_NMAX || !(fabs(gamma_p_ratio - 1.0) <= OR_CCMAX)) return -1;
+    or_bdf *s = (or_bdf *)calloc(1, sizeof(or_bdf));
+    if (!s) return -1;
+    linear_ode(&p, n, A, 0, c, &ode);
+    s->n = n;
+    s->st = st;
+    s->h = h;
+    s->gamma_p = 1.0;
+    s->crate = OR_CRATE0;
+    memcpy(s->z, z, sizeof(double) * 2 * n);
+    /* factor at gamma_P: a first call with need_j set */
+    s->need_j = 1;
+    (void)newton(s, &ode, w, l, cq, gamma_p_ratio * h / l1, e, y);
+    /* the recorded call at gamma = h / l1 reuses that matrix */
+    s->jage = 1;
+    s->page = 1;
+    s->trace = trace;
+    s->ntrace = 0;
+    *result = newton(s, &ode, w, l, cq, h / l1, e, y);
+    const int k = s->ntrace;
+    free(s);
+    return k;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -77,6 +77,10 @@ def lib():
                                               C.c_int, C.c_int, C.c_double, C.c_double, _dp, _ip]
             L.or_linear_fixed_steps.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int, _dp,
                                                 C.c_double, _dp, _dp, _dp, _dp]
+            L.or_linear_initial_step.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double]
+            L.or_linear_initial_step.restype = C.c_double
+            L.or_linear_newton.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double, _dp,
+                                           C.c_double, _dp, _ip]
             L.or_bdf_coeffs.argtypes = [C.c_int, _dp, _dp, _dp]
             L.or_err_coef_qm1.argtypes = [C.c_int, _dp]
             L.or_err_coef_qm1.restype = C.c_double
@@ -273,6 +277,28 @@ def linear_fixed_steps(A, c, q, hs, t0, z, hist):
     if rc != 0:
         raise RuntimeError("Newton did not converge")
     return z, h8, e, est
+
+
+def linear_initial_step(A, y0, rtol=1e-6, atol=1e-10, span=1e30):
+    """The integrator's starting step for y' = A y at y0."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    return lib().or_linear_initial_step(y0.size, _d(A), _d(y0), rtol, atol, span)
+
+
+def linear_newton(A, z0, z1, l1, h, gamma_p_ratio, w, cq=1.0):
+    """The integrator's modified Newton on y' = A y: returns (iterates e_k as
+    rows, outcome 0 converged / 1 failed); see or_linear_newton."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    z = np.ascontiguousarray(np.concatenate([z0, z1]), dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    tr = np.zeros(3 * n)
+    res = np.zeros(1, dtype=np.int32)
+    k = lib().or_linear_newton(n, _d(A), _d(z), l1, h, gamma_p_ratio, _d(w), cq, _d(tr), _i(res))
+    if k < 0:
+        raise ValueError("bad arguments")
+    return tr[:k * n].reshape(k, n), int(res[0])
 
 
 def bdf_coeffs(q, xi):

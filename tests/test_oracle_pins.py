@@ -508,3 +508,74 @@ def test_lu_pivot_ties_take_the_first_row():
     assert piv[0] == 1
     _, _, rc = oracle.lu_factor(np.array([[1.0, 2.0], [2.0, 4.0]]))
     assert rc == 1
+
+
+# ---------------------------------------------------------------- starting step
+def test_starting_step_closed_form_on_scalar_problems():
+    """Hairer, Norsett & Wanner's starting step (Solving ODEs I, II.4) with
+    p = 1 on y' = lam y, worked by hand. With w = rtol |y0| + atol:
+    d0 = |y0|/w, d1 = |lam y0|/w, h0 = 0.01 d0/d1 = 0.01/|lam| (both norms
+    above 1e-5), the Euler trial gives d2 = |f(y0 + h0 f0) - f0|/(w h0)
+    = lam^2 |y0|/w, and h = min(100 h0, sqrt(0.01 / max(d1, d2)), span)."""
+    # lam = -1000, y0 = 1: w = 1.0001e-6, d2 = 1e6/w dominates, h = sqrt(0.01 w / 1e6)
+    h = oracle.linear_initial_step([[-1000.0]], [1.0])
+    assert abs(h / np.sqrt(1.0001e-14) - 1) < 1e-14
+    # lam = -0.5, y0 = 2: w = 2.0001e-6, d1 = 1/w exceeds d2 = 0.5/w,
+    # h = sqrt(0.01 w) = sqrt(2.0001e-8) < 100 h0 = 2
+    h = oracle.linear_initial_step([[-0.5]], [2.0])
+    assert abs(h / np.sqrt(2.0001e-8) - 1) < 1e-14
+    # the span clips h0 and then h
+    h = oracle.linear_initial_step([[-1000.0]], [1.0], span=1e-8)
+    assert h == 1e-8
+    # y0 = 0: both norms vanish, h0 = 1e-6, and with d1 = d2 = 0 the rule takes
+    # max(1e-6, 1e-3 h0) = 1e-6
+    h = oracle.linear_initial_step([[-3.0]], [0.0])
+    assert h == 1e-6
+
+
+def test_starting_step_on_a_diagonal_system():
+    """Two decoupled modes lam = (-1000, -1), y0 = (1, 1): the WRMS norms are
+    the root-mean-squares of the two components, d1 = sqrt((1e6 + 1)/2)/w,
+    d2 = sqrt((1e12 + 1)/2)/w, h0 = 0.01 sqrt(2/(1e6 + 1))."""
+    w = 1.0001e-6
+    h0 = 0.01 * np.sqrt(2.0 / (1e6 + 1.0))
+    h1 = np.sqrt(0.01 * w / np.sqrt((1e12 + 1.0) / 2.0))
+    h = oracle.linear_initial_step(np.diag([-1000.0, -1.0]), [1.0, 1.0])
+    assert abs(h / min(100 * h0, h1) - 1) < 1e-13
+
+
+# ---------------------------------------------------------------- Newton
+def test_newton_with_a_current_matrix_is_exact_on_a_linear_problem():
+    """For y' = A y the corrector equation h A (z0 + e) - z1 - l1 e = 0 is
+    linear, and P = I - (h/l1) A is its exact Jacobian divided by -l1: the
+    first modified-Newton correction from e = 0 is the solution
+    e* = (l1 I - h A)^-1 (h A z0 - z1), and the second finds nothing left."""
+    A = np.array([[-1000.0, 1.0, 0.0], [2.0, -3.0, 0.5], [0.0, 40.0, -7.0]])
+    z0 = np.array([1.0, 0.5, 0.25])
+    z1 = np.array([0.3, -0.2, 0.1])
+    for l1, h in ((1.0, 0.01), (1.5, 0.02)):
+        want = np.linalg.solve(l1 * np.eye(3) - h * A, h * A @ z0 - z1)
+        tr, res = oracle.linear_newton(A, z0, z1, l1, h, 1.0, w=np.full(3, 1e-30))
+        np.testing.assert_allclose(tr[0], want, rtol=1e-13, atol=1e-16)
+        np.testing.assert_allclose(tr[1], want, rtol=1e-13, atol=1e-16)
+        # loose weights: the first correction already passes the convergence test
+        tr, res = oracle.linear_newton(A, z0, z1, l1, h, 1.0, w=np.full(3, 1e6))
+        assert res == 0 and tr.shape[0] == 1
+
+
+def test_stale_matrix_correction_contracts_at_its_closed_form_rate():
+    """Scalar y' = lam y with the matrix formed at gamma_P = r gamma: each
+    correction delta = c (1 - gamma_P lam)^-1 [(h lam (z0 + e) - z1)/l1 - e],
+    c = 2 / (1 + gamma/gamma_P), so the error e - e* is multiplied by
+    rho = 1 - c (1 - gamma lam) / (1 - gamma_P lam) and e_k = e* (1 - rho^k).
+    With lam = -1e4, h = 0.01, l1 = 1 (gamma lam = -100): r = 1.2 gives
+    c = 12/11, rho = 1 - (12/11)(101/121) = 119/1331; r = 0.8 gives c = 8/9,
+    rho = 1 - (8/9)(101/81) = -79/729. Tiny weights keep the convergence test
+    from stopping the three corrections."""
+    lam, h, l1, z0, z1 = -1e4, 0.01, 1.0, 0.7, -0.2
+    e_star = (h * lam * z0 - z1) / (l1 - h * lam)
+    for r, rho in ((1.2, 119.0 / 1331.0), (0.8, -79.0 / 729.0)):
+        tr, res = oracle.linear_newton([[lam]], [z0], [z1], l1, h, r, w=[1e-30])
+        assert res == 1 and tr.shape[0] == 3
+        for k in range(3):
+            assert abs(tr[k, 0] - e_star * (1 - rho ** (k + 1))) <= 1e-14 * abs(e_star)
