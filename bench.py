@@ -1,12 +1,20 @@
 """Benchmark of the per-cell burn on B300.
 
-Workload (one "step" = one burn of the whole batch): the 13-ODE synthetic
-network (12 species from 3 elements + the energy equation, 40 reversible
-reactions), 2^20 cells per GPU, T log-uniform [10, 1e4] K, n log-uniform
-[1, 1e8] cm^-3, dt = 1e10 s, rtol = 1e-6, atol = 1e-10. The headline arm is the
-FP32-iteration-matrix persistent path; the plain FP64 path on the same inputs
-is reported beside it. Inputs are reset from a device-resident copy before
-every step (inside the timed region) and L2 is flushed between steps.
+Workload (one "step" = one burn of the whole batch): the precision form on the
+13-ODE synthetic network (12 species from 3 elements + the energy equation, 40
+reversible reactions), 2^22 cells per GPU, T log-uniform [10, 1e4] K, n
+log-uniform [1, 1e8] cm^-3, dt = 1e10 s, rtol = 1e-6, atol = 1e-10. The
+headline arm is the FP32-iteration-matrix persistent path (FP32 LU refined
+with FP64 residuals, FP64 retry of the cells it cannot serve). Beside it, on
+one GPU: the FP64-matrix persistent path on the same cells (same scheduling,
+so the pair isolates the matrix precision) and the plain FP64 path (one
+thread per cell, one launch, no refill) on the 2^20-cell plain FP64 workload.
+Inputs are reset from a device-resident copy before every step (inside the
+timed region); the inputs (470 MB) exceed L2 and L2 is flushed between steps.
+
+``--config mixed`` times the batched uneven-work form instead: one persistent
+launch over 2^22 cells split evenly over Robertson (3 ODEs, t = 40), net13 and
+net33 (33 ODEs), 1 % hot cells, replayed from a captured CUDA graph.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU FP64 oracle
 on a bounded sample of the same workload instead.
@@ -28,17 +36,53 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cells/s at rtol=1e-6 (FP32-LU persistent vs FP64 plain); p50/p99 burn latency"
-N_CELLS = 1 << 20
+N_CELLS = 1 << 22          # the precision form's workload
+N_PLAIN = 1 << 20          # the plain FP64 workload
 DT = 1.0e10
-CELL_SEED = 3
+CELL_SEED = 4              # precision-form cells
+PLAIN_SEED = 3             # plain-FP64 cells
+ORACLE_SAMPLE = 131072     # cells of the oracle's timed sample (baseline and reference arm)
+PARITY_SAMPLE = 512
 
-# FP64-pipe cost model of the algorithm (operations per unit, each a fused or
-# plain FP64 arithmetic instruction; an FMA is 2 flops, anything else 1):
-# exp/log/div/sqrt/pow are charged the FP64 instruction counts of the CUDA
-# math routines the kernels call, measured once by throughput against the FMA
-# rate (exp 20, log 36, div 8). The table-driven exp costs about 11, so the
-# model slightly overstates the work; it is kept fixed so numbers compare.
-EXP_OPS, LOG_OPS, DIV_OPS = 20, 36, 8
+# ---- FP64-pipe roofline model ---------------------------------------------
+# FP64 flops per unit of work (an FMA is 2 flops, an add or a multiply 1).
+# Measured by ncu's thread-level DFMA/DADD/DMUL counters on the library's own
+# evaluation kernels (profiles/fp64_per_unit_eval_kernels.md):
+#   RHS_FLOPS_PER_REACTION   one reaction of a right-hand side: two table
+#                            exponentials and their arguments, the mass-action
+#                            products, the scatter and the energy term
+#   RHS_FLOPS_FIXED          the rest of a right-hand side (EOS temperature,
+#                            log T, 1/T, sums)
+# Counted from the code (no transcendental inside):
+#   Jacobian   a right-hand side's rates plus 22 flops per reaction for the
+#              derivatives and n (S + 1) for the EOS chain rule
+#   FP64 LU    (2/3) n^3 + n^2 / 2; an FP32 LU costs the FP64 pipe nothing
+#   solve      FP64: 2 n^2; FP32: one refinement sweep, 2 n^2 + 5 n (further
+#              sweeps are not counted, so the FP32 figure is a lower bound)
+#   attempt    (q(q+1)/2 + 2(q+1) + 3) n with q = 3, the weights' n reciprocals
+#              charged 1 flop each
+RHS_FLOPS_PER_REACTION = 51.75   # k_rates slope 38.75 (two exponentials with their arguments) + 13
+RHS_FLOPS_FIXED = 47.0           # k_rhs on net13: 2117 flops per right-hand side = 47 + 40 x 51.75
+
+
+def fp64_flops(S, R, n, stats, lu_precision):
+    """Algorithmic FP64 flops of the work the per-cell counters record."""
+    st = stats.astype(np.float64)
+    attempts = st[0] + st[1] + st[2]
+    f_rhs = RHS_FLOPS_FIXED + R * RHS_FLOPS_PER_REACTION
+    f_jac = f_rhs + 22.0 * R + n * (S + 1)
+    f_lu = (2.0 / 3.0) * n ** 3 + 0.5 * n * n if lu_precision == 64 else 0.0
+    f_solve = 2.0 * n * n if lu_precision == 64 else 2.0 * n * n + 5.0 * n
+    q = 3
+    f_step = (q * (q + 1) / 2 + 2 * (q + 1) + 3) * n + n
+    return float((st[3] * f_rhs + st[4] * f_jac + st[5] * f_lu + st[6] * f_solve + attempts * f_step).sum())
+
+
+# DRAM traffic of the burn's thread-per-cell worker per step attempt, from an
+# ncu capture of its bulk on 2^20 cells (profiles/k_burn_persistent_net13_2p20_bulk.md:
+# 2.088 TB read + written over 243.8 M attempts); the fused kernel runs the same
+# worker, and the traffic (lane state past L2) grows with attempts, not cells.
+DRAM_BYTES_PER_ATTEMPT = 8565.0
 
 # where the nvidia-smi clock samples of the timed region are written
 LOG_DIR = os.environ.get("MC_BENCH_LOG_DIR", os.path.join(tempfile.gettempdir(), "mc_bench"))
@@ -66,20 +110,6 @@ def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
 def job_throughput(cells_per_rank: int, world: int, ms: float) -> float:
     """Whole-job cells/s: the cells of every rank over the slowest rank's time."""
     return cells_per_rank * world / (ms / 1e3)
-
-
-def fp64_ops_per_cell(S, R, n, stats):
-    """FP64 operations of the work the per-cell counters record."""
-    rhs, jac, lu, newton, steps = (stats[3].astype(np.float64), stats[4].astype(np.float64),
-                                   stats[5].astype(np.float64), stats[6].astype(np.float64),
-                                   stats[0].astype(np.float64))
-    attempts = steps + stats[1] + stats[2]
-    f_rhs = S + 3 + DIV_OPS + LOG_OPS + DIV_OPS + R * (2 * EXP_OPS + 4 + 5 + 2 + 4 + 1)
-    f_jac = f_rhs + R * (16 + 6 + 10) + n * (S + 1)
-    f_lu = n * n + (2.0 / 3.0) * n ** 3 + n * DIV_OPS
-    f_solve = 2.0 * n * n + n * DIV_OPS + 3 * n + 2 * n + 1
-    f_step = 15 * n + 2 * n + n * DIV_OPS + 4 * n + 60
-    return rhs * f_rhs + jac * f_jac + lu * f_lu + newton * f_solve + attempts * f_step
 
 
 def clock_sampler_start(path):
@@ -137,6 +167,23 @@ def cpu_baseline(net, n_sample, seed):
             "sample": f"{n_sample} cells of the same workload (seed {seed}), FP64 oracle, "
                       f"{cores} threads, {dt:.1f} s; cells/s extrapolates linearly",
             "ok_fraction": float(np.mean(status == 0))}
+
+
+def parity_sample(net, cells, idx, gx, gT, gs):
+    """The oracle's verdict on sampled cells of a timed burn (tests/parity.py)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from parity import classify, compare
+    on = oracle.OracleNetwork(net)
+    o, stable, reprobe = classify(on, cells, DT, oracle.burn, index=idx, with_reprobe=True)
+    t = oracle.burn(on, cells, DT, rtol=1e-10, atol=1e-16, index=idx)
+    rep = compare(gx, gT, gs, o[0], o[1], o[2], o[3], stable=stable, tight=(t[0], t[1]), reprobe=reprobe)
+    return {"sampled_cells": int(idx.size), "pass": rep["pass"], "stable": rep["stable"],
+            "sensitive": rep["sensitive"], "reclassified": rep["reclassified"],
+            "max_rel_x_stable": rep["max_rel_x_stable"], "max_rel_T_stable": rep.get("max_rel_T_stable"),
+            "status_mismatch": rep["status_mismatch"],
+            "sensitive_err_gpu_p50_p90_max": rep.get("sensitive_err_gpu_p50_p90_max"),
+            "sensitive_err_oracle_p50_p90_max": rep.get("sensitive_err_oracle_p50_p90_max")}
 
 
 def serving_measurement(mc, n_sat=6, n_load=8, seed=7, edge_range=(16, 64)):
@@ -200,10 +247,10 @@ def run_reference(args, rank, world):
     net = network_13()
     if rank != 0:
         return
-    n_sample = int(os.environ.get("MC_REF_SAMPLE", "4096"))
+    n_sample = int(os.environ.get("MC_REF_SAMPLE", str(ORACLE_SAMPLE)))
     times = []
     for i in range(args.warmup + args.steps):
-        b = cpu_baseline(net, n_sample, seed=CELL_SEED + i)
+        b = cpu_baseline(net, n_sample, seed=CELL_SEED + 100 * i)
         if i >= args.warmup:
             times.append(n_sample / b["value"])
     ms = 1e3 * float(np.mean(times))
@@ -212,12 +259,186 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "net13 synthetic kinetics, 12 species + energy, 40 reactions; "
-                                   f"bounded sample of {n_sample} cells per step (seeds {CELL_SEED}..)",
+                                   f"bounded sample of {n_sample} cells per step (seeds {CELL_SEED} + 100 i)",
                        "n_cells_per_step": n_sample, "dt_s": DT, "rtol": 1e-6, "atol": 1e-10},
             "cpu_baseline": {"value": value, "unit": "cells/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{n_sample} cells per step"},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+MIXED_CELLS = 1 << 22
+MIXED_SEED = 6
+MIXED_DTS = (40.0, DT, DT)   # Robertson to t = 40, the energy networks over dt
+
+
+def run_mixed(args, mc, world, rank, local, stream, flush, barrier, fp64_peak, fp32_peak):
+    """The batched uneven-work form: 2^22 cells split evenly over Robertson,
+    net13 and net33 (1 % hot cells), one persistent launch captured in a CUDA
+    graph and replayed each step; inputs reset from device copies inside the
+    timed region."""
+    import torch
+    from paper_2608_06466_b300.api import to_device
+    from mc_inputs import mixed_batch
+    n = args.cells
+    batch = mixed_batch(n, seed=MIXED_SEED + 1000 * rank, hot_fraction=0.01)
+    segs, keep = [], []
+    for (net, cells, idx), dt in zip(batch["groups"], MIXED_DTS):
+        h = mc.Network(net)
+        d = to_device(cells)
+        x0 = d["x"].clone()
+        T0 = None if d["T"] is None else d["T"].clone()
+        m = cells["x"].shape[1]
+        segs.append(mc.segment(h, m, m, d["x"], d["T"], d["ndens"], d["rate_scale"], d["status"], d["stats"], dt=dt))
+        keep.append((h, d, x0, T0, net, cells))
+    opts = mc.mc_burn_opts_default(lu_precision=32)
+    g = mc.mc_graph_create(segs, opts, DT)
+
+    def reset():
+        for (h, d, x0, T0, net, cells) in keep:
+            d["x"].copy_(x0)
+            if T0 is not None:
+                d["T"].copy_(T0)
+
+    def step():
+        reset()
+        g.launch(stream)
+
+    ms, per, launches, clocks = timed_steps(step, args.steps, args.warmup, stream, flush, barrier, rank, local, True)
+    ms = max_over_ranks(ms, world, "cuda")
+    flops, attempts, ok = 0.0, 0.0, 0
+    results = []
+    for (h, d, x0, T0, net, cells) in keep:
+        st = d["stats"].cpu().numpy()
+        flops += fp64_flops(net.n_species, net.n_reactions, net.n_ode, st, 32)
+        attempts += float((st[0].astype(np.int64) + st[1] + st[2]).sum())
+        s = d["status"].cpu().numpy()
+        ok += int((s == 0).sum())
+        results.append((d["x"].cpu().numpy(), None if d["T"] is None else d["T"].cpu().numpy(), s))
+    # end to end: inputs from pinned host memory, graph replay, results back
+    hosts = []
+    for (h, d, x0, T0, net, cells) in keep:
+        hx = torch.from_numpy(np.ascontiguousarray(cells["x"])).pin_memory()
+        hT = None if T0 is None else torch.from_numpy(np.ascontiguousarray(cells["T"])).pin_memory()
+        ox = torch.empty_like(hx).pin_memory()
+        oT = None if hT is None else torch.empty_like(hT).pin_memory()
+        os_ = torch.empty(d["status"].shape, dtype=torch.int32).pin_memory()
+        hosts.append((hx, hT, ox, oT, os_))
+    e2e_ms = []
+    h2d = d2h = 0
+    for i in range(1 + max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (h, d, x0, T0, net, cells), (hx, hT, ox, oT, os_) in zip(keep, hosts):
+            d["x"].copy_(hx, non_blocking=True)
+            if hT is not None:
+                d["T"].copy_(hT, non_blocking=True)
+        g.launch(stream)
+        for (h, d, x0, T0, net, cells), (hx, hT, ox, oT, os_) in zip(keep, hosts):
+            ox.copy_(d["x"], non_blocking=True)
+            if oT is not None:
+                oT.copy_(d["T"], non_blocking=True)
+            os_.copy_(d["status"], non_blocking=True)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    for (hx, hT, ox, oT, os_) in hosts:
+        h2d += hx.numel() * 8 + (0 if hT is None else hT.numel() * 8)
+        d2h += ox.numel() * 8 + (0 if oT is None else oT.numel() * 8) + os_.numel() * 4
+    g.close()
+    e2e_v = job_throughput(n, world, max_over_ranks(float(np.mean(e2e_ms)), world, "cuda"))
+    parity, cpu = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        parity = []
+        for (h, d, x0, T0, net, cells), (gx, gT, gs), dt in zip(keep, results, MIXED_DTS):
+            sys.path.insert(0, os.path.join(ROOT, "tests"))
+            from parity import classify, compare
+            m = cells["x"].shape[1]
+            idx = np.sort(np.random.default_rng(2).choice(m, 128, replace=False))
+            on = oracle.OracleNetwork(net)
+            o, stable, rp = classify(on, cells, dt, oracle.burn, index=idx, with_reprobe=True)
+            t = oracle.burn(on, cells, dt, rtol=1e-10, atol=1e-16, index=idx)
+            rep = compare(gx[:, idx], None if gT is None else gT[idx], gs[idx], *o, stable=stable,
+                          tight=(t[0], t[1]), reprobe=rp)
+            parity.append({"network": net.name, "sampled_cells": 128, "pass": rep["pass"], "stable": rep["stable"],
+                           "max_rel_x_stable": rep["max_rel_x_stable"], "status_mismatch": rep["status_mismatch"]})
+        # the oracle on a bounded sample of each segment (a third of the sample each)
+        cores = os.cpu_count() or 1
+        sample = 3 * 4096
+        t0 = time.perf_counter()
+        for (h, d, x0, T0, net, cells), dt in zip(keep, MIXED_DTS):
+            sub = {k: (None if v is None else (v[..., :sample // 3] if k != "hot" else v[:sample // 3]))
+                   for k, v in cells.items()}
+            oracle.burn(oracle.OracleNetwork(net), sub, dt, nthreads=cores)
+        el = time.perf_counter() - t0
+        cpu = {"value": sample / el, "unit": "cells/s", "cores": cores, "kind": "oracle",
+               "sample": f"{sample} cells, a third of each network's segment, FP64 oracle, {cores} threads, "
+                         f"{el:.1f} s; cells/s extrapolates linearly"}
+    achieved = flops / (ms / 1e3) / 1e12
+    return {
+        "metric": METRIC, "value": job_throughput(n, world, ms), "unit": "cells/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched uneven work: Robertson (3 ODEs, t = 40) + net13 (13 ODEs) + net33 "
+                               "(33 ODEs, 4 elements, 120 reactions), a third each, 1 % hot cells T log-U[1e4, 1e5] K",
+                   "n_cells_per_gpu": n, "seed": MIXED_SEED + 1000 * rank, "dt_s": list(MIXED_DTS),
+                   "rtol": 1e-6, "atol": 1e-10, "lu_precision": 32,
+                   "variant": "one persistent launch over all networks (cost-ordered queues, hand-off and "
+                              "warp-per-cell record pass), CUDA graph replay",
+                   "l2": "inputs exceed L2 and L2 is flushed between steps",
+                   "parallelism": f"independent shards x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak,
+                     "traffic": None, "peak_source": "FP64 FMA rate measured in this run (mc_probe_fma_rate)",
+                     "attempts": attempts},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_v, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches), "clocks": clocks, "status_ok_fraction": ok / n,
+        "parity_sample": parity, "per_step_ms": per,
+    }
+
+
+def _build_if_missing():
+    if not os.path.exists(os.path.join(ROOT, "paper_2608_06466_b300", "libmc.so")):
+        # a fresh checkout: build the library (loading the build script by path,
+        # since importing the package needs the library)
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("_mc_build",
+                                                      os.path.join(ROOT, "paper_2608_06466_b300", "build.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build()
+
+
+def timed_steps(step, steps, warmup, stream, flush, barrier, rank, local, sample_clocks):
+    """W untimed and K timed steps, CUDA events on the launching stream, a
+    barrier and a device synchronize on both sides, L2 flushed before each."""
+    import torch
+    import paper_2608_06466_b300 as mc
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    mc.mc_launch_count(reset=True)
+    path = os.path.join(LOG_DIR, f"bench_clocks_r{rank}.csv")
+    proc, fh = clock_sampler_start(path) if sample_clocks else (None, None)
+    per = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    launches = mc.mc_launch_count()
+    clocks = clock_sampler_stop(proc, fh, path, local) if sample_clocks else None
+    return float(np.mean(per)), per, launches, clocks
 
 
 def main():
@@ -226,9 +447,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="precision", choices=["precision", "mixed"])
     ap.add_argument("--cells", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP64 comparison arms")
     ap.add_argument("--serving", action="store_true",
                     help="add the serving-loop measurement (AMR-box requests, a few minutes)")
     ap.add_argument("--no-serving", action="store_true", help="no serving measurement (the default)")
@@ -242,15 +464,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    if not os.path.exists(os.path.join(ROOT, "paper_2608_06466_b300", "libmc.so")):
-        # a fresh checkout: build the library (loading the build script by path,
-        # since importing the package needs the library)
-        import importlib.util
-        spec = importlib.util.spec_from_file_location("_mc_build",
-                                                      os.path.join(ROOT, "paper_2608_06466_b300", "build.py"))
-        mod = importlib.util.module_from_spec(spec)
-        spec.loader.exec_module(mod)
-        mod.build()
+    _build_if_missing()
     import paper_2608_06466_b300 as mc
     from paper_2608_06466_b300.api import to_device
     from mc_inputs import network_13, synthetic_cells
@@ -264,69 +478,79 @@ def main():
         if world > 1:
             dist.barrier()
 
+    os.makedirs(LOG_DIR, exist_ok=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    fp64_peak, fp32_peak = mc.mc_probe_fma_rate()
+    if args.config == "mixed":
+        line = run_mixed(args, mc, world, rank, local, stream, flush, barrier, fp64_peak, fp32_peak)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     net = network_13()
     h = mc.Network(net)
     n = args.cells
     cells = synthetic_cells(net, n, seed=shard_seed(rank))
     d = to_device(cells)
     x0, T0 = d["x"].clone(), d["T"].clone()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
     opts32 = mc.mc_burn_opts_default(lu_precision=32, variant=mc.MC_VARIANT_PERSISTENT)
+    opts64p = mc.mc_burn_opts_default(lu_precision=64, variant=mc.MC_VARIANT_PERSISTENT)
     opts64 = mc.mc_burn_opts_default(lu_precision=64, variant=mc.MC_VARIANT_PLAIN)
 
-    def one_step(opts):
+    def burn(opts):
         d["x"].copy_(x0)
         d["T"].copy_(T0)
         mc.mc_burn_batch(h, opts, n, DT, d["x"], n, d["T"], d["ndens"], None, d["status"], d["stats"], stream)
 
-    def timed(opts, steps, warmup, sample_clocks=False):
-        for _ in range(warmup):
-            one_step(opts)
-        torch.cuda.synchronize()
-        barrier()
-        torch.cuda.synchronize()
-        mc.mc_launch_count(reset=True)
-        proc, fh = clock_sampler_start(os.path.join(LOG_DIR, f"bench_clocks_r{rank}.csv")) \
-            if sample_clocks else (None, None)
-        total = 0.0
-        per = []
-        for _ in range(steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            one_step(opts)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            per.append(ms)
-            total += ms
-        torch.cuda.synchronize()
-        barrier()
-        launches = mc.mc_launch_count()
-        clocks = clock_sampler_stop(proc, fh, os.path.join(LOG_DIR, f"bench_clocks_r{rank}.csv"),
-                                    local) if sample_clocks else None
-        ms = max_over_ranks(total / steps, world, "cuda")
-        return ms, per, launches, clocks
-
-    os.makedirs(LOG_DIR, exist_ok=True)
-    fp64_peak, fp32_peak = mc.mc_probe_fma_rate()
-
-    ms32, per32, launches, clocks = timed(opts32, args.steps, args.warmup, sample_clocks=True)
+    ms32, per32, launches, clocks = timed_steps(lambda: burn(opts32), args.steps, args.warmup, stream, flush,
+                                                barrier, rank, local, sample_clocks=True)
+    ms32 = max_over_ranks(ms32, world, "cuda")
+    gx, gT = d["x"].cpu().numpy(), d["T"].cpu().numpy()
     status = d["status"].cpu().numpy()
     stats = d["stats"].cpu().numpy()
-    ops = float(fp64_ops_per_cell(net.n_species, net.n_reactions, net.n_ode, stats).sum())
+    flops = fp64_flops(net.n_species, net.n_reactions, net.n_ode, stats, 32)
+    attempts = float((stats[0].astype(np.int64) + stats[1] + stats[2]).sum())
     value = job_throughput(n, world, ms32)
 
-    plain = None
-    if not args.no_plain:
-        ms64, _, _, _ = timed(opts64, 1, 1)
-        st64 = d["stats"].cpu().numpy()
-        ops64 = float(fp64_ops_per_cell(net.n_species, net.n_reactions, net.n_ode, st64).sum())
-        plain = {"value": job_throughput(n, world, ms64), "unit": "cells/s", "ms_per_step": ms64,
-                 "fp64_tflops_algorithmic": 2 * ops64 / (ms64 / 1e3) / 1e12,
-                 "ok_fraction": float(np.mean(d["status"].cpu().numpy() == 0))}
+    # FP64 comparison arms: same scheduling with the FP64 matrix on the same
+    # cells, and the plain one-thread-per-cell FP64 path on the plain
+    # workload's 2^20 cells; one timed step each after a small warm-up burn
+    arms = None
+    if not args.no_plain and world == 1:
+        small = min(n, 4096)
+        for o in (opts64p, opts64):
+            mc.mc_burn_batch(h, o, small, DT, d["x"], n, d["T"], d["ndens"], None, d["status"], d["stats"], stream)
+        ms64p, _, _, _ = timed_steps(lambda: burn(opts64p), 1, 0, stream, flush, barrier, rank, local, False)
+        st64p = d["stats"].cpu().numpy()
+        cells_p = synthetic_cells(net, N_PLAIN, seed=PLAIN_SEED)
+        dp = to_device(cells_p)
+        xp0, Tp0 = dp["x"].clone(), dp["T"].clone()
+
+        def burn_plain():
+            dp["x"].copy_(xp0)
+            dp["T"].copy_(Tp0)
+            mc.mc_burn_batch(h, opts64, N_PLAIN, DT, dp["x"], N_PLAIN, dp["T"], dp["ndens"], None, dp["status"],
+                             dp["stats"], stream)
+
+        ms64, _, _, _ = timed_steps(burn_plain, 1, 0, stream, flush, barrier, rank, local, False)
+        st64 = dp["stats"].cpu().numpy()
+        arms = {
+            "fp64_persistent": {
+                "value": n / (ms64p / 1e3), "unit": "cells/s", "ms_per_step": ms64p, "cells": n,
+                "fp64_tflops_algorithmic": fp64_flops(net.n_species, net.n_reactions, net.n_ode, st64p, 64)
+                / (ms64p / 1e3) / 1e12,
+                "note": "same cells and scheduling as the headline, FP64 iteration matrix"},
+            "fp64_plain": {
+                "value": N_PLAIN / (ms64 / 1e3), "unit": "cells/s", "ms_per_step": ms64, "cells": N_PLAIN,
+                "fp64_tflops_algorithmic": fp64_flops(net.n_species, net.n_reactions, net.n_ode, st64, 64)
+                / (ms64 / 1e3) / 1e12,
+                "ok_fraction": float(np.mean(dp["status"].cpu().numpy() == 0)),
+                "note": f"plain FP64 workload: 2^20 cells (seed {PLAIN_SEED}), one thread per cell, one launch"},
+        }
+        del dp
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     xh = torch.from_numpy(np.ascontiguousarray(cells["x"])).pin_memory()
@@ -348,55 +572,44 @@ def main():
     h2d = (net.n_species + 2) * 8 * n
     d2h = (net.n_species + 1) * 8 * n + 4 * n
 
-    # sampled parity of the timed results against the oracle
     parity = None
-    if rank == 0 and not args.no_cpu_baseline:
-        sys.path.insert(0, os.path.join(ROOT, "tests"))
-        import oracle
-        from parity import classify, compare
-        idx = np.sort(np.random.default_rng(1).choice(n, 128, replace=False))
-        one_step(opts32)
-        torch.cuda.synchronize()
-        on = oracle.OracleNetwork(net)
-        (o, stable) = classify(on, cells, DT, oracle.burn, index=idx, perturb=1e-9)
-        t = oracle.burn(on, cells, DT, rtol=1e-10, atol=1e-16, index=idx)
-        gx = d["x"].cpu().numpy()[:, idx]
-        gT = d["T"].cpu().numpy()[idx]
-        gs = d["status"].cpu().numpy()[idx]
-        rep = compare(gx, gT, gs, o[0], o[1], o[2], o[3], stable=stable, tight=(t[0], t[1]), fp32_matrix=True)
-        parity = {"sampled_cells": 128, "pass": rep["pass"], "stable": rep["stable"],
-                  "max_rel_x_stable": rep["max_rel_x_stable"], "status_mismatch": rep["status_mismatch"],
-                  "stable_within_1e-5_frac": rep["stable_within_1e-5_frac"]}
-
+    cpu = None
     serving = None
+    if rank == 0 and not args.no_cpu_baseline:
+        idx = np.sort(np.random.default_rng(1).choice(n, PARITY_SAMPLE, replace=False))
+        parity = parity_sample(net, cells, idx, gx[:, idx], gT[idx], status[idx])
     if rank == 0 and args.serving and not args.no_serving:
         serving = serving_measurement(mc)
-
-    cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(net, int(os.environ.get("MC_CPU_SAMPLE", "262144")), CELL_SEED)
+        cpu = cpu_baseline(net, int(os.environ.get("MC_CPU_SAMPLE", str(ORACLE_SAMPLE))), CELL_SEED)
 
     if rank == 0:
-        achieved = 2 * ops / (ms32 / 1e3) / 1e12
+        achieved = flops / (ms32 / 1e3) / 1e12
+        traffic = None if DRAM_BYTES_PER_ATTEMPT is None else DRAM_BYTES_PER_ATTEMPT * attempts
         line = {
             "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "net13 synthetic kinetics: 12 species from 3 elements + energy equation "
-                                   "(13 ODEs), 40 reversible reactions, ideal gas gamma=5/3",
-                       "n_cells_per_gpu": n, "dt_s": DT, "rtol": 1e-6, "atol": 1e-10,
+            "config": {"workload": "precision form: net13 synthetic kinetics, 12 species from 3 elements + energy "
+                                   "equation (13 ODEs), 40 reversible reactions, ideal gas gamma=5/3",
+                       "n_cells_per_gpu": n, "cell_seed": shard_seed(rank), "dt_s": DT, "rtol": 1e-6, "atol": 1e-10,
                        "T_K": "log-uniform [10, 1e4]", "n_cm3": "log-uniform [1, 1e8]",
-                       "lu_precision": 32, "variant": "persistent (cost-ordered queue, one cooperative launch with hand-off)", "max_steps": 100000,
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"independent shards x{world}"},
+                       "lu_precision": 32, "variant": "persistent (cost-ordered queue, one cooperative launch "
+                                                      "with hand-off, FP64 retry pass)",
+                       "max_steps": 100000,
+                       "l2": "inputs exceed L2 (470 MB) and L2 is flushed between steps (256 MB write)",
+                       "parallelism": f"independent shards x{world}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak, "traffic": None,
+                         "frac": achieved / fp64_peak, "traffic": traffic,
                          "peak_source": "FP64 FMA rate measured in this run (mc_probe_fma_rate)",
-                         "fp32_fma_peak_tflops": fp32_peak},
+                         "model": "FP64 flops per unit from ncu counters on the evaluation kernels x the run's "
+                                  "per-cell counters",
+                         "attempts": attempts, "fp32_fma_peak_tflops": fp32_peak},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clocks,
-            "fp64_plain": plain,
+            "fp64_arms": arms,
             "status_ok_fraction": float(np.mean(status == 0)),
             "parity_sample": parity,
             "serving": serving,

@@ -120,7 +120,14 @@ typedef struct {
     int32_t straggler_steps;/* persistent variant: a cell still running after this many
                                attempts is finished by a whole warp (0 = default 2048,
                                -1 = never) */
+    int32_t jacobian;       /* MC_JAC_ANALYTIC (default) or MC_JAC_FD: forward differences,
+                               column j = (f(y + d_j e_j) - f(y)) / d_j,
+                               d_j = 2^-26 (|y_j| + atol / rtol) (one of the "Jacobian
+                               approximations" of the paper's retry, Software design ¶3) */
 } mc_burn_opts;
+
+#define MC_JAC_ANALYTIC 0
+#define MC_JAC_FD 1
 
 void mc_burn_opts_default(mc_burn_opts *opts);
 
@@ -153,6 +160,46 @@ mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t
                         const double *rate_scale, int32_t *status, int32_t *stats,
                         void *stream);
 
+/* One rung of a retry ladder: the options of one attempt. */
+typedef struct {
+    mc_burn_opts opts;    /* tolerances, step cap, order, matrix precision, Jacobian */
+    int32_t method;       /* MC_METHOD_BDF (the VODE-style integrator) or MC_METHOD_RKC */
+} mc_rung;
+
+#define MC_METHOD_BDF 0
+#define MC_METHOD_RKC 1   /* explicit Runge-Kutta-Chebyshev, order 2 (Sommeijer, Shampine &
+                             Verwer 1998): the integrator the paper offers beside VODE
+                             (Software design section, paragraphs 2 and 4); a ladder of one
+                             RKC rung is a plain RKC burn */
+
+/* Burn with a retry ladder (paper: Software design section, paragraph 3 --
+ * a zone whose integration fails is retried with different tolerances or
+ * Jacobian approximations before the failure is passed back). Every cell is
+ * burned with rung 0; a cell whose status is MC_CELL_MAX_STEPS,
+ * MC_CELL_H_UNDERFLOW, MC_CELL_CONV_FAIL or MC_CELL_NONFINITE is burned again
+ * from its inputs with the next rung, up to n_rungs (1..8). Outputs, status
+ * and stats come from the cell's last attempt; rung[c] (int32, may be NULL)
+ * receives the rung that produced them. Cell arrays as in mc_burn_batch, device
+ * memory only; the failed cells of each rung are compacted into a list that
+ * the next rung's launch reads on the device (no host synchronisation).
+ * Asynchronous on stream. Errors: MC_E_INVALID, MC_E_NOMEM, MC_E_CUDA. */
+mc_status mc_burn_ladder(const mc_network *net, const mc_rung *rungs, int32_t n_rungs, int64_t n_cells, double dt,
+                         double *x, int64_t ld, double *T, const double *ndens, const double *rate_scale,
+                         int32_t *status, int32_t *stats, int32_t *rung, void *stream);
+
+/* Burn with a constant source term added to every cell's right-hand side:
+ * dy/dt = f(y) + s, s = source[i * ld + c] for ODE component i (the species
+ * rates, then the energy rate du/dt in eV per unit density and second, with
+ * u = (sum x) k_B T / (gamma - 1)). This is the burn inside a step coupled by
+ * spectral deferred corrections, where the advective change of each cell is
+ * held fixed over the burn (paper: Software design section, paragraph 4, the
+ * second coupling mode beside operator splitting). Arguments, layout and
+ * errors otherwise as mc_burn_batch (host or device arrays, all alike);
+ * source is required. */
+mc_status mc_burn_batch_sdc(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells, double dt,
+                            double *x, int64_t ld, double *T, const double *ndens, const double *rate_scale,
+                            const double *source, int32_t *status, int32_t *stats, void *stream);
+
 /* Rate coefficients of every reaction at n temperatures T[c] (device
  * arrays): kf[r * ld + c], kr[r * ld + c] (kr = 0 for irreversible reactions),
  * computed by the burn's own device code (including its table-driven
@@ -180,11 +227,15 @@ mc_status mc_network_rhs(const mc_network *net, int64_t n, const double *y, int6
  *   - cell arrays must be device memory, and n_cells <= MC_NOALLOC_MAX_CELLS
  *     (larger batches are rejected with MC_E_INVALID before any work);
  *   - its scratch is a fixed file-scope device array of 256 bytes plus 4 bytes
- *     per cell of that maximum (about 4 MB), held by every GPU that loads the
- *     library until the process exits; no straggler hand-off is done;
- *   - the first call on each device looks up the array's device address
- *     (with that device current); make that first call before any stream
- *     capture;
+ *     per cell of that maximum (about 4 MB); no straggler hand-off is done;
+ *   - the array belongs to the library's device code, which CUDA loads on a
+ *     device lazily: the first call on each device (made with that device
+ *     current) loads it and looks up the array's device address, and that
+ *     first burn may also make the driver reserve local memory for the burn
+ *     kernels' per-thread stacks. So make one warm-up call per device before
+ *     an arena takes the rest of device memory, and before any stream
+ *     capture; the array and the reservation then stay until the process
+ *     exits, and later calls allocate nothing (mc_alloc_count does not move);
  *   - every call shares the one array: it clears what must start at zero on
  *     the stream, but calls whose work overlaps on the GPU (different streams,
  *     or another thread) race and corrupt each other's results. */
@@ -194,7 +245,9 @@ mc_status mc_burn_batch_noalloc(const mc_network *net, const mc_burn_opts *opts,
                                 const double *rate_scale, int32_t *status, int32_t *stats, void *stream);
 
 /* One segment of a mixed batch: cells that share a network, laid out as in
- * mc_burn_batch (device pointers). */
+ * mc_burn_batch (device pointers), and their own burn interval dt (seconds;
+ * 0 takes the dt passed to the call), so networks with different time scales
+ * share one launch. */
 typedef struct {
     const mc_network *net;
     int64_t n_cells;
@@ -205,6 +258,7 @@ typedef struct {
     const double *rate_scale;
     int32_t *status;
     int32_t *stats;
+    double dt;
 } mc_segment;
 
 /* Burn several segments (different networks, uneven stiffness) in ONE
@@ -237,15 +291,19 @@ mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts, int64_t n
 
 /* ---------------------------------------------------------------- serving */
 /* A server (paper: state resident in GPU memory, Software design section,
- * paragraph 3) admits burn requests in arrival order while the bytes of
- * admitted request state stay within hbm_budget_bytes (a request counts
- * (n_species + 2) doubles and one int per cell), copies each admitted
- * request's state into pooled device memory, burns it with the persistent
- * kernel on one of the server's 8 streams and copies the results back to the
- * caller's buffers. Requests that arrive while others are on the GPU start as
- * soon as memory and a stream are free, so their work overlaps on the device
- * (continuous batching); a host thread does admission and completion, and no
- * device code waits on the host. */
+ * paragraph 3) admits burn requests in arrival order while the device bytes
+ * they need stay within hbm_budget_bytes: each request's state in pooled
+ * device memory ((n_species + 2) doubles and one int per cell, see
+ * mc_request_bytes) plus the growth of the library scratch of the stream it
+ * runs on (the server keeps 8 streams; scratch is per stream and never
+ * shrinks, so each stream's high-water mark stays charged). An admitted
+ * request's state is copied into the pool, burned with its own options on
+ * its stream, its failed cells counted on the device, and the results copied
+ * back to the caller's buffers. Requests that arrive while others are on the
+ * GPU start as soon as memory and a stream are free, so their work overlaps on
+ * the device (continuous batching); a host thread does admission and
+ * completion, the GPU work is enqueued outside the server's lock, and no device
+ * code waits on the host. Server calls are thread-safe. */
 typedef struct {
     int32_t state;          /* MC_PENDING or MC_OK */
     int32_t n_failed;       /* cells with status != MC_CELL_OK */
@@ -253,19 +311,29 @@ typedef struct {
     double t_submit;        /* seconds on the server's monotonic clock */
     double t_admit;
     double t_done;
+    double gpu_start;       /* seconds from the server's creation on the GPU's clock: */
+    double gpu_end;         /* when the request's work started and ended on its stream */
 } mc_request_info;
 
+/* opts: the server's default options for requests that pass none. */
 mc_status mc_server_create(int32_t device, uint64_t hbm_budget_bytes, const mc_burn_opts *opts,
                            mc_server **out);
-/* Queue a request. Cell arrays as in mc_burn_batch (host or device memory;
- * rate_scale is not supported here). The caller must not touch them until
- * mc_request_poll reports MC_OK. Never blocks on the GPU. Errors:
- * MC_E_BUDGET if the request alone exceeds the budget, MC_E_INVALID. */
-mc_status mc_request_submit(mc_server *srv, const mc_network *net, int64_t n_cells, double dt,
-                            double *x, int64_t ld, double *T, const double *ndens,
+/* Bytes a request of n_cells charges against the budget: its pooled state and
+ * the stream scratch its burn needs (either pointer may be NULL). */
+mc_status mc_request_bytes(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
+                           uint64_t *state_bytes, uint64_t *scratch_bytes);
+/* Queue a request (paper: Software design section, paragraph 3, one zone's
+ * burn handed to the GPU). opts may be NULL (the server's). Cell arrays as in
+ * mc_burn_batch (host or device memory; rate_scale is not supported here).
+ * The caller must not touch them until mc_request_poll reports MC_OK. Never
+ * blocks on the GPU. Errors: MC_E_BUDGET if the request alone exceeds the
+ * budget, MC_E_INVALID, MC_E_BUSY while the server shuts down. */
+mc_status mc_request_submit(mc_server *srv, const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
+                            double dt, double *x, int64_t ld, double *T, const double *ndens,
                             int32_t *status, uint64_t *req_id);
 /* MC_PENDING while in flight, MC_OK once results are in the caller's buffers
- * (info filled in either case when non-NULL), MC_E_NOTFOUND otherwise. */
+ * (info filled in either case when non-NULL); the request's own error code and
+ * message if its work failed; MC_E_NOTFOUND for an unknown id. */
 mc_status mc_request_poll(mc_server *srv, uint64_t req_id, mc_request_info *info);
 /* Wait (bounded by timeout_s) until every submitted request is done. */
 mc_status mc_server_drain(mc_server *srv, double timeout_s);
@@ -277,6 +345,10 @@ const char *mc_last_error(void);
 int32_t mc_version(void);
 /* Kernel launches issued by this thread since the last reset (for accounting). */
 int64_t mc_launch_count(int32_t reset);
+/* Device and pinned-host allocations the library has made in this process,
+ * all threads (network uploads, scratch growth, host-array staging, serving
+ * pool, autotuner copies). mc_burn_batch_noalloc never adds to it. */
+int64_t mc_alloc_count(void);
 /* Measure the fused multiply-add rate (TFLOP/s, 2 flops per FMA) of the
  * current device in FP64 and FP32 with dependent-free FMA chains over every SM
  * (about 10 ms each): the ceiling this ALU-bound burn is reported against.

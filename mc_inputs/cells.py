@@ -69,3 +69,18 @@ def mixed_batch(n_cells: int, seed: int = 6, hot_fraction: float = 0.01) -> dict
             cells = synthetic_cells(net, len(idx), seed=seed * 7 + 1 + g, hot_fraction=hot_fraction)
         groups.append((net, cells, idx))
     return {"net_id": net_id, "groups": groups}
+
+
+def synthetic_sources(net: Network, cells: dict, dt: float, seed: int, scale: float = 0.1) -> np.ndarray:
+    """Constant per-cell sources [n_ode, n] of the size an advective coupling
+    term has: each species' source moves it by up to ``scale`` of its initial
+    fraction over dt (uniform in [-scale, scale], relative); the energy
+    component's source is uniform in [-scale, scale] x 1e-4 T / dt (eV per unit
+    density and second; 1e-4 T is of the order of u for fractions summing to 1)."""
+    rng = np.random.default_rng(seed)
+    x = np.asarray(cells["x"], dtype=np.float64)
+    ref = [x]
+    if net.energy_eq:
+        ref.append(1e-4 * np.asarray(cells["T"], dtype=np.float64)[None, :])
+    ref = np.concatenate(ref, axis=0)
+    return rng.uniform(-scale, scale, size=ref.shape) * ref / dt

@@ -42,18 +42,24 @@ class mc_network_desc(C.Structure):
 class mc_burn_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_order", C.c_int32),
                 ("max_steps", C.c_int32), ("lu_precision", C.c_int32), ("variant", C.c_int32),
-                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("straggler_steps", C.c_int32)]
+                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("straggler_steps", C.c_int32),
+                ("jacobian", C.c_int32)]
+
+
+class mc_rung(C.Structure):
+    _fields_ = [("opts", mc_burn_opts), ("method", C.c_int32)]
 
 
 class mc_segment(C.Structure):
     _fields_ = [("net", C.c_void_p), ("n_cells", C.c_int64), ("ld", C.c_int64), ("x", C.c_void_p),
                 ("T", C.c_void_p), ("ndens", C.c_void_p), ("rate_scale", C.c_void_p),
-                ("status", C.c_void_p), ("stats", C.c_void_p)]
+                ("status", C.c_void_p), ("stats", C.c_void_p), ("dt", C.c_double)]
 
 
 class mc_request_info(C.Structure):
     _fields_ = [("state", C.c_int32), ("n_failed", C.c_int32), ("n_cells", C.c_int64),
-                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("gpu_start", C.c_double), ("gpu_end", C.c_double)]
 
 
 def _sig(name, res, args):
@@ -72,6 +78,12 @@ _sig("mc_network_n_ode", C.c_int32, [C.c_void_p])
 _sig("mc_burn_batch", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p,
                                   C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p])
+_sig("mc_burn_batch_sdc", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p,
+                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p])
+_sig("mc_burn_ladder", C.c_int32, [C.c_void_p, C.POINTER(mc_rung), C.c_int32, C.c_int64, C.c_double, C.c_void_p,
+                                   C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p])
 _sig("mc_burn_batch_noalloc", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p,
                                           C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p])
@@ -82,14 +94,18 @@ _sig("mc_graph_create", C.c_int32, [C.POINTER(mc_segment), C.c_int32, C.POINTER(
 _sig("mc_graph_launch", C.c_int32, [C.c_void_p, C.c_void_p])
 _sig("mc_graph_destroy", C.c_int32, [C.c_void_p])
 _sig("mc_server_create", C.c_int32, [C.c_int32, C.c_uint64, C.POINTER(mc_burn_opts), C.POINTER(C.c_void_p)])
-_sig("mc_request_submit", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int64,
-                                      C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)])
+_sig("mc_request_submit", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double,
+                                      C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.POINTER(C.c_uint64)])
+_sig("mc_request_bytes", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.POINTER(C.c_uint64),
+                                     C.POINTER(C.c_uint64)])
 _sig("mc_request_poll", C.c_int32, [C.c_void_p, C.c_uint64, C.POINTER(mc_request_info)])
 _sig("mc_server_drain", C.c_int32, [C.c_void_p, C.c_double])
 _sig("mc_server_destroy", C.c_int32, [C.c_void_p])
 _sig("mc_last_error", C.c_char_p, [])
 _sig("mc_version", C.c_int32, [])
 _sig("mc_launch_count", C.c_int64, [C.c_int32])
+_sig("mc_alloc_count", C.c_int64, [])
 _sig("mc_network_rates", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                      C.c_void_p])
 _sig("mc_network_rhs", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -193,6 +209,34 @@ def mc_burn_batch(net: Network, opts: mc_burn_opts | None, n_cells: int, dt: flo
                                    _stream_ptr(stream)), "mc_burn_batch")
 
 
+def mc_burn_batch_sdc(net: Network, opts: mc_burn_opts | None, n_cells: int, dt: float, x, ld: int, T, ndens,
+                      rate_scale, source, status, stats, stream=None) -> int:
+    """mc_burn_batch with a constant source [n_ode][ld] added to the right-hand side."""
+    o = opts if opts is not None else mc_burn_opts_default()
+    return check(lib.mc_burn_batch_sdc(net.handle, C.byref(o), int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T),
+                                       _ptr(ndens), _ptr(rate_scale), _ptr(source), _ptr(status), _ptr(stats),
+                                       _stream_ptr(stream)), "mc_burn_batch_sdc")
+
+
+MC_JAC_ANALYTIC, MC_JAC_FD = 0, 1
+MC_METHOD_BDF, MC_METHOD_RKC = 0, 1
+
+
+def rung(method=MC_METHOD_BDF, **opts) -> mc_rung:
+    """One retry-ladder rung: mc_burn_opts fields as keywords, and the method."""
+    return mc_rung(mc_burn_opts_default(**opts), int(method))
+
+
+def mc_burn_ladder(net: Network, rungs, n_cells: int, dt: float, x, ld: int, T, ndens, rate_scale, status, stats,
+                   rung_out=None, stream=None) -> int:
+    """Burn with a retry ladder (device arrays); rung_out [n] int32 receives
+    the rung that produced each cell's outputs."""
+    arr = (mc_rung * len(rungs))(*rungs)
+    return check(lib.mc_burn_ladder(net.handle, arr, len(rungs), int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T),
+                                    _ptr(ndens), _ptr(rate_scale), _ptr(status), _ptr(stats), _ptr(rung_out),
+                                    _stream_ptr(stream)), "mc_burn_ladder")
+
+
 MC_NOALLOC_MAX_CELLS = 1 << 20
 
 
@@ -206,9 +250,10 @@ def mc_burn_batch_noalloc(net: Network, opts: mc_burn_opts | None, n_cells: int,
                                            _stream_ptr(stream)), "mc_burn_batch_noalloc")
 
 
-def segment(net: Network, n_cells, ld, x, T, ndens, rate_scale, status, stats) -> mc_segment:
+def segment(net: Network, n_cells, ld, x, T, ndens, rate_scale, status, stats, dt=0.0) -> mc_segment:
+    """One segment of a mixed burn; dt = 0 takes the call's dt."""
     return mc_segment(net.handle.value, int(n_cells), int(ld), _ptr(x), _ptr(T), _ptr(ndens), _ptr(rate_scale),
-                      _ptr(status), _ptr(stats))
+                      _ptr(status), _ptr(stats), float(dt))
 
 
 def mc_burn_mixed(segs, opts: mc_burn_opts | None, dt: float, stream=None) -> int:
@@ -253,11 +298,20 @@ class Server:
               "mc_server_create")
         self.handle = h
 
-    def submit(self, net: Network, n_cells, dt, x, ld, T, ndens, status) -> int:
+    def submit(self, net: Network, n_cells, dt, x, ld, T, ndens, status, opts: mc_burn_opts | None = None) -> int:
         rid = C.c_uint64()
-        check(lib.mc_request_submit(self.handle, net.handle, int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T),
-                                    _ptr(ndens), _ptr(status), C.byref(rid)), "mc_request_submit")
+        check(lib.mc_request_submit(self.handle, net.handle, C.byref(opts) if opts is not None else None,
+                                    int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T), _ptr(ndens), _ptr(status),
+                                    C.byref(rid)), "mc_request_submit")
         return rid.value
+
+    @staticmethod
+    def request_bytes(net: Network, n_cells, opts: mc_burn_opts | None = None):
+        """(state bytes, stream scratch bytes) a request charges against the budget."""
+        a, b = C.c_uint64(), C.c_uint64()
+        check(lib.mc_request_bytes(net.handle, C.byref(opts) if opts is not None else None, int(n_cells),
+                                   C.byref(a), C.byref(b)), "mc_request_bytes")
+        return a.value, b.value
 
     def poll(self, req_id: int):
         info = mc_request_info()
@@ -310,3 +364,7 @@ def mc_probe_fma_rate():
 
 def mc_launch_count(reset: bool = False) -> int:
     return int(lib.mc_launch_count(1 if reset else 0))
+
+
+def mc_alloc_count() -> int:
+    return int(lib.mc_alloc_count())

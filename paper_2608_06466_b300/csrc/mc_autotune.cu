@@ -102,9 +102,9 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
   const int64_t n = n_sample;
   double *wx = nullptr, *wT = nullptr;
   int32_t *ws = nullptr;
-  cudaError_t e = cudaMalloc(&wx, sizeof(double) * net->S * n);
-  if (e == cudaSuccess && T) e = cudaMalloc(&wT, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&ws, sizeof(int32_t) * n);
+  cudaError_t e = dev_malloc((void **)&wx, sizeof(double) * net->S * n);
+  if (e == cudaSuccess && T) e = dev_malloc((void **)&wT, sizeof(double) * n);
+  if (e == cudaSuccess) e = dev_malloc((void **)&ws, sizeof(int32_t) * n);
   if (e != cudaSuccess) {
     cudaFree(wx);
     cudaFree(wT);

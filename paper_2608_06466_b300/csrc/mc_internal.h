@@ -33,6 +33,11 @@ constexpr int RMAX_REACT = 512;   // largest reaction count accepted
 constexpr int MAX_QUEUES = 16;    // persistent queue counters per device
 
 mc_status set_error(mc_status code, const char *fmt, ...);
+// Every device or pinned-host allocation of the library goes through these,
+// so mc_alloc_count can report them.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+cudaError_t host_malloc_pinned(void **p, size_t bytes);
 mc_status cuda_error(cudaError_t e, const char *what);
 void count_launch(int64_t k);
 DNet dnet_of(const mc_network *net);
@@ -44,11 +49,18 @@ void scratch_free(void *h);
 mc_status scratch_get(int dev, int64_t retry_cells, unsigned long long **next, uint32_t **rcount,
                       int32_t **retry);
 mc_status burn_device(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st);
+// Burn with the explicit Runge-Kutta-Chebyshev integrator (mc_rkc.cu).
+mc_status burn_rkc_device(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st);
 mc_status burn_device_scratch(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st,
                               unsigned long long *next, uint32_t *rcount, int32_t *retry, bool allow_strag);
 mc_status check_batch(const mc_network *net, int64_t n_cells, double dt, double *x, int64_t ld, double *T,
                       const double *ndens, const double *rate_scale, int32_t *status, int32_t *stats,
                       bool *on_dev);
+
+// Device bytes a burn of n cells of this network with these options makes the
+// library scratch of its stream grow to (queue counters, FP32 retry list, cost
+// order, straggler records), for budgeted admission.
+size_t burn_scratch_bytes(const mc_network *net, const mc_burn_opts &o, int64_t n);
 
 // launch shape chosen for a network and options
 struct Tuned {
@@ -76,6 +88,10 @@ struct DevAttrCache {
 template <int N, typename LT>
 mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int variant, int threads,
                      int blocks_per_sm, int strag_steps, unsigned long long *next, cudaStream_t st);
+
+// Library-owned retry-ladder lists of the current stream's scratch set: two
+// lists of n cells each (lists, lists + n) and their two counts.
+mc_status ladder_scratch(int dev, int64_t n, int32_t **lists, uint32_t **counts);
 
 // Library-owned record buffer for straggler hand-off (grown on demand) and its
 // claim counter, on the current device.

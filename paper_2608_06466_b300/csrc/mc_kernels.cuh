@@ -4,7 +4,7 @@
 // divergence the paper's Software design section, paragraph 3, names).
 #pragma once
 
-#include "mc_device.cuh"
+#include "mc_coop.cuh"
 
 namespace mc {
 
@@ -17,13 +17,41 @@ struct CellArgs {
   double *T;
   const double *nd;
   const double *ks;
+  const double *src;        // optional constant source [n_ode][ld]
   int32_t *status;
   int32_t *stats;
   const int32_t *index;     // optional cell list: entry k is cell index[k]
   const uint32_t *n_dev;    // optional device-side count overriding n_cells
   int32_t *retry;           // FP32 pass: cells to redo in FP64 (nullptr = none)
   uint32_t *retry_count;
+  uint32_t retry_mask;      // statuses (bit 1 << status) that go to retry
+  int32_t *lretry;          // retry ladder: cells for the next rung (nullptr = none)
+  uint32_t *lretry_count;
+  uint32_t lretry_mask;     // statuses that go to lretry
+  int32_t *rung;            // retry ladder: rung that wrote each cell's outputs, or nullptr
+  int32_t rung_id;
 };
+
+// statuses an FP32-matrix pass hands to its FP64 retry pass
+constexpr uint32_t FP32_RETRY_MASK = (1u << CELL_CONV_FAIL) | (1u << CELL_H_UNDERFLOW) | (1u << CELL_RETRY64);
+// statuses a retry-ladder rung hands to the next rung
+constexpr uint32_t LADDER_MASK = (1u << CELL_MAX_STEPS) | (1u << CELL_H_UNDERFLOW) | (1u << CELL_CONV_FAIL) |
+                                 (1u << CELL_NONFINITE) | (1u << CELL_RETRY64);
+
+// Where a finished cell goes: 1 = the FP64 retry list, 2 = the next rung's
+// list, 0 = its outputs are written (status adjusted when nothing takes it).
+__device__ __forceinline__ int route_of(const CellArgs &a, int &status) {
+  const uint32_t bit = 1u << status;
+  if (a.retry && (a.retry_mask & bit)) return 1;
+  if (a.lretry && (a.lretry_mask & bit)) return 2;
+  if (status == CELL_RETRY64) status = CELL_CONV_FAIL;  // no retry pass to take it
+  return 0;
+}
+
+__device__ __forceinline__ void push_list(int32_t *list, uint32_t *count, int64_t c) {
+  const uint32_t k = atomicAdd(count, 1u);
+  list[k] = (int32_t)c;
+}
 
 __device__ __forceinline__ int64_t cell_of(const CellArgs &a, int64_t k) {
   return a.index ? (int64_t)a.index[k] : k;
@@ -66,6 +94,7 @@ __device__ void load_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a, in
   L.cin.nd = nd;
   L.cin.ks = a.ks ? a.ks + c : nullptr;
   L.cin.ks_ld = a.ld;
+  L.cin.src = a.src ? a.src + c : nullptr;
   if (net.energy) {
     if (!(X > 0.0) || !isfinite(X)) good = false;
     L.z[0][S] = X * KB_EV * T / net.gm1;
@@ -88,17 +117,18 @@ __device__ void load_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a, in
   L.phase = PH_F0;
 }
 
-// Write cell results. FP32-matrix runs hand Newton and step-size failures to
-// an FP64 retry list instead of writing them (the inputs stay in place).
+// Write cell results. FP32-matrix runs hand Newton and step-size failures, and
+// cells whose refined FP32 solves could not reach the FP64 solve, to an FP64
+// retry list instead of writing them, and a retry-ladder rung hands its
+// retryable failures to the next rung's list (the inputs stay in place).
 template <int N, typename LT>
 __device__ void store_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a) {
   const int64_t c = L.cell;
   const int S = net.S;
-  if (a.retry && (L.status == CELL_CONV_FAIL || L.status == CELL_H_UNDERFLOW)) {
-    const uint32_t k = atomicAdd(a.retry_count, 1u);
-    a.retry[k] = (int32_t)c;
-    return;
-  }
+  const int route = route_of(a, L.status);
+  if (route == 1) { push_list(a.retry, a.retry_count, c); return; }
+  if (route == 2) { push_list(a.lretry, a.lretry_count, c); return; }
+  if (a.rung) a.rung[c] = a.rung_id;
   const bool rejected = (L.status == CELL_BAD_INPUT && L.m < 0);
   if (!rejected) {
     double X = 0.0;
@@ -127,6 +157,7 @@ __global__ void __launch_bounds__(256) k_burn_plain(DNet net, Opts o, CellArgs a
   while (L.phase != PH_DONE) {
     const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
     advance(L, net, o, ok);
+    if (L.todo == TD_MATRIX) matrix_thread(L, net, o);
     run_stages(L, net, o);
   }
   store_cell(L, net, a);
@@ -164,15 +195,19 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
 // Persistent worker loop over one queue of cells. `next` counts cells handed
 // out (reset to 0 before the launch). Every lane of the warp runs the loop, so
 // the warp-wide votes are safe; the loop returns once the queue is drained and
-// every lane's cell is stored or handed off.
+// every lane's cell is stored or handed off. One loop trip: one right-hand
+// side for every busy lane, the warp-cooperative matrix work of the lanes
+// that wait for it (coop_matrix, in the warp's workspace sh), then the step
+// logic's stages.
 template <int N, typename LT>
 __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs &a,
-                                  unsigned long long *next, const StragArgs &sa) {
+                                  unsigned long long *next, const StragArgs &sa, const WSh<LT> &sh) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t total = count_of(a);
   Lane<N, LT> L;
   L.phase = PH_IDLE;
+  L.todo = TD_NONE;
   bool active = true;
   for (;;) {
     if (L.phase == PH_DONE) {
@@ -197,6 +232,9 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
     if (busy) {
       const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
       advance(L, net, o, ok);
+    }
+    coop_matrix<N, LT>(L, net, o, sh);
+    if (busy) {
       run_stages(L, net, o);
       if (sa.rec && L.phase == PH_NEWTON && L.m == 0 && L.attempts >= sa.threshold && !L.kept) {
         const uint32_t k = atomicAdd(sa.count, 1u);
@@ -214,8 +252,11 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
 
 template <int N, typename LT>
 __global__ void __launch_bounds__(256) k_burn_persistent(DNet net, Opts o, CellArgs a,
-                                                         unsigned long long *next, StragArgs sa) {
-  persistent_worker<N, LT>(net, o, a, next, sa);
+                                                         unsigned long long *next, StragArgs sa,
+                                                         int smem_per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const WSh<LT> sh = wsh_carve<N, LT>(smem + (threadIdx.x >> 5) * (size_t)smem_per_warp, net.R);
+  persistent_worker<N, LT>(net, o, a, next, sa, sh);
 }
 
 // ---- cost order of the cell queue -------------------------------------------
@@ -252,6 +293,7 @@ __device__ int cost_bucket(const DNet &net, const Opts &o, const CellArgs &a, in
   if (!(cin.nd > 0.0) || !isfinite(cin.nd) || !(T > 0.0) || !isfinite(T)) good = false;
   cin.ks = a.ks ? a.ks + c : nullptr;
   cin.ks_ld = a.ld;
+  cin.src = a.src ? a.src + c : nullptr;
   cin.lnT = 0.0;
   cin.invT = 0.0;
   if (net.energy) {

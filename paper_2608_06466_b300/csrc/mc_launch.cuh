@@ -61,8 +61,27 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
       if (e == cudaSuccess) e = cudaMemsetAsync(sa.flag, 0, sizeof(uint32_t) * (size_t)ncap, st);
       if (e != cudaSuccess) return cuda_error(e, "straggler list reset");
     }
+    // warp workspace of the cooperative matrix work; blocks shrink if the
+    // workspaces of a full block would not fit the shared memory of a block
+    const int per_warp_p = (int)wsh_bytes<N, LT>(d.R);
+    int smem_max = 0;
+    e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_error(e, "shared memory limit");
+    const int pthreads = std::max(32, std::min(threads, 32 * (smem_max / per_warp_p)));
+    const int psmem = per_warp_p * (pthreads / 32);
+    static thread_local DevAttrCache configured_p;
+    if (configured_p.below(dev, psmem)) {
+      e = cudaFuncSetAttribute(k_burn_persistent<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+      if (e != cudaSuccess) return cuda_error(e, "persistent kernel smem attribute");
+      configured_p.raise(dev, psmem);
+    }
+    if (pthreads != threads) {
+      blocks = (int64_t)sms * blocks_per_sm * (threads / pthreads);
+      if (!a.n_dev) blocks = std::min<int64_t>(blocks, (a.n_cells + pthreads - 1) / pthreads);
+      if (blocks < 1) blocks = 1;
+    }
     if (!sa.rec) {
-      k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
+      k_burn_persistent<N, LT><<<(unsigned)blocks, pthreads, psmem, st>>>(d, o, a, next, sa, per_warp_p);
     } else {
       const int per_warp = (int)wsh_bytes<N, LT>(d.R);
       bool fused = false;
@@ -106,7 +125,8 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
           fused = true;
         }
       }
-      if (!fused) k_burn_persistent<N, LT><<<(unsigned)blocks, threads, 0, st>>>(d, o, a, next, sa);
+      if (!fused)
+        k_burn_persistent<N, LT><<<(unsigned)blocks, pthreads, psmem, st>>>(d, o, a, next, sa, per_warp_p);
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_error(e, "burn kernel launch");
       count_launch(1);

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -36,6 +38,25 @@ mc_status mc::cuda_error(cudaError_t e, const char *what) {
 
 void mc::count_launch(int64_t k) { g_launches += k; }
 
+static std::atomic<int64_t> g_allocs{0};
+
+cudaError_t mc::dev_malloc(void **p, size_t bytes) {
+  g_allocs.fetch_add(1);
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t mc::dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+  g_allocs.fetch_add(1);
+  return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t mc::host_malloc_pinned(void **p, size_t bytes) {
+  g_allocs.fetch_add(1);
+  return cudaMallocHost(p, bytes);
+}
+
+extern "C" int64_t mc_alloc_count(void) { return g_allocs.load(); }
+
 extern "C" const char *mc_last_error(void) { return g_err.c_str(); }
 extern "C" int32_t mc_version(void) { return 1; }
 extern "C" int64_t mc_launch_count(int32_t reset) {
@@ -55,6 +76,7 @@ extern "C" void mc_burn_opts_default(mc_burn_opts *o) {
   o->block_threads = 0;
   o->blocks_per_sm = 0;
   o->straggler_steps = 0;
+  o->jacobian = MC_JAC_ANALYTIC;
 }
 
 // ---------------------------------------------------------------- networks
@@ -104,8 +126,8 @@ extern "C" mc_status mc_network_create(const mc_network_desc *d, mc_network **ou
   net->par_h = par;
   cudaError_t e = cudaGetDevice(&net->device);
   if (e != cudaSuccess) { delete net; return cuda_error(e, "cudaGetDevice"); }
-  e = cudaMalloc(&net->side_d, sizeof(int4) * side.size());
-  if (e == cudaSuccess) e = cudaMalloc(&net->par_d, sizeof(RxPar) * par.size());
+  e = dev_malloc((void **)&net->side_d, sizeof(int4) * side.size());
+  if (e == cudaSuccess) e = dev_malloc((void **)&net->par_d, sizeof(RxPar) * par.size());
   if (e == cudaSuccess) e = cudaMemcpy(net->side_d, side.data(), sizeof(int4) * side.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(net->par_d, par.data(), sizeof(RxPar) * par.size(), cudaMemcpyHostToDevice);
   // occurrence lists in the order the right-hand side scatters: per reaction
@@ -126,9 +148,9 @@ extern "C" mc_status mc_network_create(const mc_network_desc *d, mc_network **ou
   // 2^(j/64) for the table-driven exponential, rounded once from extended precision
   double tab[64];
   for (int j = 0; j < 64; ++j) tab[j] = (double)exp2l((long double)j / 64.0L);
-  if (e == cudaSuccess) e = cudaMalloc(&net->exptab_d, sizeof tab);
+  if (e == cudaSuccess) e = dev_malloc((void **)&net->exptab_d, sizeof tab);
   if (e == cudaSuccess) e = cudaMemcpy(net->exptab_d, tab, sizeof tab, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&net->csr_d, sizeof(int) * csr.size());
+  if (e == cudaSuccess) e = dev_malloc((void **)&net->csr_d, sizeof(int) * csr.size());
   if (e == cudaSuccess) e = cudaMemcpy(net->csr_d, csr.data(), sizeof(int) * csr.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(net->side_d);
@@ -185,6 +207,8 @@ struct DevScratch {
   size_t rec_bytes = 0;
   void *order = nullptr;                // cost order: list, bucket bytes, histogram
   int64_t order_cap = 0;
+  void *ladder = nullptr;               // retry ladder: two cell lists and their counts
+  int64_t ladder_cap = 0;
 };
 std::mutex g_scratch_mu;
 std::map<std::pair<int, uintptr_t>, DevScratch> g_scratch;
@@ -225,6 +249,7 @@ void mc::scratch_free(void *h) {
   cudaFree(d->rec);
   cudaFree(d->rec_count);
   cudaFree(d->order);
+  cudaFree(d->ladder);
   delete d;
 }
 
@@ -235,7 +260,7 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
   DevScratch &s = scratch_of(dev);
   cudaError_t e;
   if (!s.next) {
-    e = cudaMalloc(&s.next, (sizeof(unsigned long long) + sizeof(uint32_t)) * MAX_QUEUES);
+    e = dev_malloc((void **)&s.next, (sizeof(unsigned long long) + sizeof(uint32_t)) * MAX_QUEUES);
     if (e != cudaSuccess) return cuda_error(e, "scratch allocation");
     s.retry_count = (uint32_t *)(s.next + MAX_QUEUES);
   }
@@ -244,7 +269,7 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
     s.retry = nullptr;
     s.retry_cap = 0;
     if (e != cudaSuccess) return cuda_error(e, "scratch grow sync");
-    e = cudaMalloc(&s.retry, sizeof(int32_t) * retry_cells);
+    e = dev_malloc((void **)&s.retry, sizeof(int32_t) * retry_cells);
     if (e != cudaSuccess) return cuda_error(e, "retry list allocation");
     s.retry_cap = retry_cells;
   }
@@ -261,7 +286,7 @@ mc_status mc::straggler_scratch(size_t bytes, void **rec, uint32_t **count) {
   DevScratch &s = scratch_of(dev);
   cudaError_t e;
   if (!s.rec_count) {
-    e = cudaMalloc(&s.rec_count, 256);
+    e = dev_malloc((void **)&s.rec_count, 256);
     if (e != cudaSuccess) return cuda_error(e, "straggler counter allocation");
   }
   if (bytes > s.rec_bytes) {
@@ -269,12 +294,29 @@ mc_status mc::straggler_scratch(size_t bytes, void **rec, uint32_t **count) {
     s.rec = nullptr;
     s.rec_bytes = 0;
     if (e != cudaSuccess) return cuda_error(e, "straggler grow sync");
-    e = cudaMalloc(&s.rec, bytes);
+    e = dev_malloc((void **)&s.rec, bytes);
     if (e != cudaSuccess) return cuda_error(e, "straggler record allocation");
     s.rec_bytes = bytes;
   }
   *rec = s.rec;
   *count = s.rec_count;
+  return MC_OK;
+}
+
+mc_status mc::ladder_scratch(int dev, int64_t n, int32_t **lists, uint32_t **counts) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  DevScratch &s = scratch_of(dev);
+  if (n > s.ladder_cap) {
+    cudaError_t e = retire(s.ladder);
+    s.ladder = nullptr;
+    s.ladder_cap = 0;
+    if (e != cudaSuccess) return cuda_error(e, "ladder grow sync");
+    e = dev_malloc(&s.ladder, 256 + sizeof(int32_t) * 2 * (size_t)n);
+    if (e != cudaSuccess) return cuda_error(e, "ladder list allocation");
+    s.ladder_cap = n;
+  }
+  *counts = (uint32_t *)s.ladder;
+  *lists = (int32_t *)((char *)s.ladder + 256);
   return MC_OK;
 }
 
@@ -288,7 +330,7 @@ mc_status mc::order_scratch(int dev, int64_t n, int32_t **index, uint8_t **bkt, 
     s.order = nullptr;
     s.order_cap = 0;
     if (e != cudaSuccess) return cuda_error(e, "order grow sync");
-    e = cudaMalloc(&s.order, list + bytes + sizeof(uint32_t) * ORDER_BUCKETS);
+    e = dev_malloc((void **)&s.order, list + bytes + sizeof(uint32_t) * ORDER_BUCKETS);
     if (e != cudaSuccess) return cuda_error(e, "order buffer allocation");
     s.order_cap = n;
   }
@@ -345,6 +387,8 @@ mc_status mc::check_opts(const mc_burn_opts *opts, mc_burn_opts *o) {
     return set_error(MC_E_INVALID, "block_threads must be a multiple of 32 up to 1024");
   if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) return set_error(MC_E_INVALID, "blocks_per_sm must be 0..32");
   if (o->straggler_steps < -1) return set_error(MC_E_INVALID, "straggler_steps must be -1, 0 or positive");
+  if (o->jacobian != MC_JAC_ANALYTIC && o->jacobian != MC_JAC_FD)
+    return set_error(MC_E_INVALID, "jacobian must be MC_JAC_ANALYTIC or MC_JAC_FD");
   return MC_OK;
 }
 
@@ -357,13 +401,14 @@ mc_status mc::burn_device_scratch(const mc_network *net, const mc_burn_opts &ob,
                                   bool allow_strag) {
   Tuned tu = autotune_pick(net, ob);
   if (!allow_strag) tu.strag_steps = 0;
-  Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps};
+  Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps, ob.jacobian == MC_JAC_FD ? 1 : 0};
   const DNet d = dnet_of(net);
   if (ob.lu_precision == 64)
     return dispatch<double>(net, d, o, a0, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);
   CellArgs a = a0;
   a.retry = retry;
   a.retry_count = rcount;
+  a.retry_mask = FP32_RETRY_MASK;
   cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_error(e, "retry counter reset");
   mc_status s = dispatch<float>(net, d, o, a, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);
@@ -395,7 +440,7 @@ mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const C
     uint32_t *hist;
     s = order_scratch(dev, a0.n_cells, &order, &bkt, &hist);
     if (s != MC_OK) return s;
-    s = order_cells(net, Opts{ob.rtol, ob.atol, ob.max_order, ob.max_steps}, a0, order, bkt, hist, st);
+    s = order_cells(net, Opts{ob.rtol, ob.atol, ob.max_order, ob.max_steps, 0}, a0, order, bkt, hist, st);
     if (s != MC_OK) return s;
     a.index = order;
   }
@@ -428,10 +473,11 @@ mc_status mc::check_batch(const mc_network *net, int64_t n_cells, double dt, dou
   return MC_OK;
 }
 
-extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
-                                   double dt, double *x, int64_t ld, double *T, const double *ndens,
-                                   const double *rate_scale, int32_t *status, int32_t *stats,
-                                   void *stream) {
+namespace {
+
+mc_status burn_batch_impl(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells, double dt, double *x,
+                          int64_t ld, double *T, const double *ndens, const double *rate_scale, const double *source,
+                          int32_t *status, int32_t *stats, void *stream) {
   mc_burn_opts o;
   mc_status s = check_opts(opts, &o);
   if (s != MC_OK) return s;
@@ -439,6 +485,7 @@ extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *op
   s = check_batch(net, n_cells, dt, x, ld, T, ndens, rate_scale, status, stats, &on_dev);
   if (s != MC_OK) return s;
   if (n_cells == 0) return MC_OK;
+  if (source && is_device_ptr(source) != on_dev) return set_error(MC_E_INVALID, "mix of host and device arrays");
   cudaStream_t st = (cudaStream_t)stream;
   CellArgs a{};
   a.n_cells = n_cells;
@@ -449,6 +496,7 @@ extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *op
     a.T = T;
     a.nd = ndens;
     a.ks = rate_scale;
+    a.src = source;
     a.status = status;
     a.stats = stats;
     return burn_device(net, o, a, st);
@@ -457,10 +505,11 @@ extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *op
   const int64_t nc = n_cells;
   const size_t bx = sizeof(double) * net->S * nc, b1 = sizeof(double) * nc;
   const size_t bks = rate_scale ? sizeof(double) * net->R * nc : 0;
+  const size_t bsr = source ? sizeof(double) * net->n * nc : 0;
   const size_t bst = sizeof(int32_t) * nc, bsx = stats ? sizeof(int32_t) * MC_NSTAT * nc : 0;
   char *buf = nullptr;
-  const size_t total = bx + (T ? b1 : 0) + (ndens ? b1 : 0) + bks + bst + bsx + 256 * 8;
-  cudaError_t e = cudaMallocAsync((void **)&buf, total, st);
+  const size_t total = bx + (T ? b1 : 0) + (ndens ? b1 : 0) + bks + bsr + bst + bsx + 256 * 9;
+  cudaError_t e = dev_malloc_async((void **)&buf, total, st);
   if (e != cudaSuccess) return cuda_error(e, "staging allocation");
   size_t off = 0;
   auto take = [&](size_t b) { char *p = buf + off; off += (b + 255) & ~(size_t)255; return p; };
@@ -468,6 +517,7 @@ extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *op
   a.T = T ? (double *)take(b1) : nullptr;
   a.nd = ndens ? (const double *)take(b1) : nullptr;
   a.ks = rate_scale ? (const double *)take(bks) : nullptr;
+  a.src = source ? (const double *)take(bsr) : nullptr;
   a.status = (int32_t *)take(bst);
   a.stats = stats ? (int32_t *)take(bsx) : nullptr;
   a.ld = nc;
@@ -479,6 +529,7 @@ extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *op
   if (e == cudaSuccess && T) e = h2d(a.T, T, 1);
   if (e == cudaSuccess && ndens) e = h2d((void *)a.nd, ndens, 1);
   if (e == cudaSuccess && rate_scale) e = h2d((void *)a.ks, rate_scale, net->R);
+  if (e == cudaSuccess && source) e = h2d((void *)a.src, source, net->n);
   if (e != cudaSuccess) { cudaFreeAsync(buf, st); return cuda_error(e, "host to device copy"); }
   s = burn_device(net, o, a, st);
   if (s != MC_OK) { cudaFreeAsync(buf, st); return s; }
@@ -494,5 +545,111 @@ extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *op
   if (e != cudaSuccess) return cuda_error(e, "device to host copy");
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "mc_burn_batch host round trip");
+  return MC_OK;
+}
+
+}  // namespace
+
+extern "C" mc_status mc_burn_batch(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
+                                   double dt, double *x, int64_t ld, double *T, const double *ndens,
+                                   const double *rate_scale, int32_t *status, int32_t *stats,
+                                   void *stream) {
+  return burn_batch_impl(net, opts, n_cells, dt, x, ld, T, ndens, rate_scale, nullptr, status, stats, stream);
+}
+
+extern "C" mc_status mc_burn_batch_sdc(const mc_network *net, const mc_burn_opts *opts, int64_t n_cells,
+                                       double dt, double *x, int64_t ld, double *T, const double *ndens,
+                                       const double *rate_scale, const double *source, int32_t *status,
+                                       int32_t *stats, void *stream) {
+  if (!source && n_cells > 0) return set_error(MC_E_INVALID, "mc_burn_batch_sdc: source is required");
+  return burn_batch_impl(net, opts, n_cells, dt, x, ld, T, ndens, rate_scale, source, status, stats, stream);
+}
+
+// ---------------------------------------------------------------- scratch size
+namespace {
+template <typename LT>
+size_t lane_bytes(int n) {
+  if (n <= 3) return sizeof(Lane<3, LT>);
+  if (n <= 8) return sizeof(Lane<8, LT>);
+  if (n <= 13) return sizeof(Lane<13, LT>);
+  if (n <= 16) return sizeof(Lane<16, LT>);
+  if (n <= 24) return sizeof(Lane<24, LT>);
+  if (n <= 33) return sizeof(Lane<33, LT>);
+  return sizeof(Lane<NMAX_ODE, LT>);
+}
+}  // namespace
+
+size_t mc::burn_scratch_bytes(const mc_network *net, const mc_burn_opts &o, int64_t n) {
+  size_t b = 2048;                                   // queue counters, retry count, record counts
+  if (o.lu_precision == 32) b += sizeof(int32_t) * (size_t)n;  // FP64 retry list
+  const Tuned tu = autotune_pick(net, o);
+  if (tu.variant != MC_VARIANT_PLAIN)
+    b += 5 * (size_t)n + 512 + sizeof(uint32_t) * ORDER_BUCKETS;  // cost order
+  if (tu.variant == MC_VARIANT_PERSISTENT && tu.strag_steps > 0 && tu.strag_steps < o.max_steps) {
+    const size_t lane = o.lu_precision == 32 ? lane_bytes<float>(net->n) : lane_bytes<double>(net->n);
+    const int64_t rec_max = (int64_t)((2ull << 30) / lane);
+    const int64_t cap = std::min<int64_t>(rec_max, std::max<int64_t>(256, n / 8));
+    b += ((lane * (size_t)cap + 255) & ~(size_t)255) + sizeof(uint32_t) * (size_t)cap;
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------- retry ladder
+extern "C" mc_status mc_burn_ladder(const mc_network *net, const mc_rung *rungs, int32_t n_rungs, int64_t n_cells,
+                                    double dt, double *x, int64_t ld, double *T, const double *ndens,
+                                    const double *rate_scale, int32_t *status, int32_t *stats, int32_t *rung,
+                                    void *stream) {
+  if (!rungs || n_rungs < 1 || n_rungs > 8) return set_error(MC_E_INVALID, "mc_burn_ladder: 1..8 rungs");
+  std::vector<mc_burn_opts> ro(n_rungs);
+  for (int k = 0; k < n_rungs; ++k) {
+    mc_status s = check_opts(&rungs[k].opts, &ro[k]);
+    if (s != MC_OK) return s;
+    if (rungs[k].method != MC_METHOD_BDF && rungs[k].method != MC_METHOD_RKC)
+      return set_error(MC_E_INVALID, "mc_burn_ladder: rung %d: unknown method", k);
+  }
+  bool on_dev = true;
+  mc_status s = check_batch(net, n_cells, dt, x, ld, T, ndens, rate_scale, status, stats, &on_dev);
+  if (s != MC_OK) return s;
+  if (n_cells == 0) return MC_OK;
+  if (!on_dev || (rung && !is_device_ptr(rung)))
+    return set_error(MC_E_INVALID, "mc_burn_ladder: cell arrays must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  scratch_stream(st);
+  int32_t *lists;
+  uint32_t *cnt;
+  s = ladder_scratch(dev, n_cells, &lists, &cnt);
+  if (s != MC_OK) return s;
+  CellArgs base{};
+  base.n_cells = n_cells;
+  base.ld = ld;
+  base.dt = dt;
+  base.x = x;
+  base.T = T;
+  base.nd = ndens;
+  base.ks = rate_scale;
+  base.status = status;
+  base.stats = stats;
+  base.rung = rung;
+  for (int k = 0; k < n_rungs; ++k) {
+    CellArgs a = base;
+    a.rung_id = k;
+    const int cur = k & 1, nxt = cur ^ 1;
+    if (k > 0) {
+      // the previous rung's failures, counted on the device
+      a.index = lists + cur * n_cells;
+      a.n_dev = cnt + cur;
+    }
+    if (k + 1 < n_rungs) {
+      cudaError_t e = cudaMemsetAsync(cnt + nxt, 0, sizeof(uint32_t), st);
+      if (e != cudaSuccess) return cuda_error(e, "ladder list reset");
+      a.lretry = lists + nxt * n_cells;
+      a.lretry_count = cnt + nxt;
+      a.lretry_mask = LADDER_MASK;
+    }
+    s = (rungs[k].method == MC_METHOD_RKC) ? burn_rkc_device(net, ro[k], a, st) : burn_device(net, ro[k], a, st);
+    if (s != MC_OK) return s;
+  }
   return MC_OK;
 }

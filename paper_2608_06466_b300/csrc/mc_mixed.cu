@@ -40,17 +40,43 @@ mc_status validate_segments(const mc_segment *segs, int32_t nseg, int dev) {
       return set_error(MC_E_INVALID, "segment %d: bad network or sizes", s);
     if (g.n_cells > 0 && (!g.x || !g.status || (g.net->energy && !g.T)))
       return set_error(MC_E_INVALID, "segment %d: x, status (and T for energy networks) are required", s);
+    if (!(g.dt >= 0.0) || !std::isfinite(g.dt))
+      return set_error(MC_E_INVALID, "segment %d: dt must be finite and not negative", s);
     if (g.net->device != dev) return set_error(MC_E_INVALID, "segment %d: network on another device", s);
   }
   return MC_OK;
 }
 
-// Queue resets and kernels of one mixed burn on stream st (capturable).
-mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts &ob, double dt,
-                       cudaStream_t st) {
-  int dev = 0, sms = 148;
+// Hand-off threshold and record capacity of a thread-per-cell segment of n
+// cells (the single-network path's defaults).
+constexpr int MIXED_STRAG_STEPS = 2048;
+
+int64_t mixed_rec_cap(int64_t n) { return std::max<int64_t>(256, n / 8); }
+
+template <int N, typename LT>
+size_t rec_bytes(int64_t cap) {
+  return (sizeof(Lane<N, LT>) * (size_t)cap + 255) & ~(size_t)255;
+}
+
+// Straggler record bytes of every thread-per-cell segment, laid out one after
+// the other (FP32 pass only takes hand-offs in the FP32 matrix form).
+size_t mixed_rec_total(const mc_segment *segs, int32_t nseg, int lu) {
+  size_t t = 0;
+  for (int s = 0; s < nseg; ++s) {
+    const int b = bucket_of(segs[s].net->n);
+    const int64_t cap = mixed_rec_cap(segs[s].n_cells);
+    if (b == 3) t += lu == 32 ? rec_bytes<3, float>(cap) : rec_bytes<3, double>(cap);
+    if (b == 13) t += lu == 32 ? rec_bytes<13, float>(cap) : rec_bytes<13, double>(cap);
+  }
+  return t;
+}
+
+// Grow every scratch buffer a mixed burn on stream st uses (queue counters,
+// retry lists, cost order, straggler records), so that the launch itself
+// neither allocates nor synchronises (it may then be captured).
+mc_status mixed_reserve(const mc_segment *segs, int32_t nseg, const mc_burn_opts &ob, cudaStream_t st) {
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t total = 0;
   for (int s = 0; s < nseg; ++s) total += segs[s].n_cells;
   unsigned long long *next;
@@ -59,47 +85,164 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
   scratch_stream(st);
   mc_status rs = scratch_get(dev, ob.lu_precision == 32 ? total : 0, &next, &rcount, &retry);
   if (rs != MC_OK) return rs;
+  int32_t *order;
+  uint8_t *bkt;
+  uint32_t *hist;
+  rs = order_scratch(dev, std::max<int64_t>(1, total), &order, &bkt, &hist);
+  if (rs != MC_OK) return rs;
+  const size_t rb = mixed_rec_total(segs, nseg, ob.lu_precision);
+  if (rb > 0) {
+    void *rec;
+    uint32_t *cnt;
+    rs = straggler_scratch(rb, &rec, &cnt);
+    if (rs != MC_OK) return rs;
+  }
+  return MC_OK;
+}
+
+template <int N, typename LT>
+mc_status launch_records(const DNet &d, const Opts &o, const CellArgs &a, const StragArgs &sa,
+                         unsigned long long *next, int sms, cudaStream_t st) {
+  const int per_warp = (int)wsh_bytes<N, LT>(d.R);
+  static thread_local DevAttrCache configured;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured.below(dev, per_warp)) {
+    cudaError_t e = cudaFuncSetAttribute(k_burn_straggler<N, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         per_warp);
+    if (e != cudaSuccess) return cuda_error(e, "mixed straggler smem attribute");
+    configured.raise(dev, per_warp);
+  }
+  const int wblocks = std::max(1, std::min(sms * 16, (int)sa.cap));
+  k_burn_straggler<N, LT><<<wblocks, 32, per_warp, st>>>(d, o, a, (const Lane<N, LT> *)sa.rec, sa.count, sa.cap,
+                                                          nullptr, next, per_warp);
+  count_launch(1);
+  return MC_OK;
+}
+
+// One pass of the mixed kernel in matrix precision LT: cost-ordered queues,
+// the persistent launch with hand-off, then the warp-per-cell pass over each
+// thread-per-cell segment's records.
+template <typename LT>
+mc_status mixed_pass(const mc_segment *segs, MixedArgs m, const Opts &o, int blocks, int msmem, bool handoff,
+                     unsigned long long *next, uint32_t *rcnt, char *rec, int sms, cudaStream_t st) {
+  const int nseg = m.nseg;
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long) * 2 * MIXED_MAX_SEGS, st);
+  if (e == cudaSuccess && handoff) e = cudaMemsetAsync(rcnt, 0, sizeof(uint32_t) * 4 * MIXED_MAX_SEGS, st);
+  if (e != cudaSuccess) return cuda_error(e, "mixed queue reset");
+  size_t off = 0;
+  for (int s = 0; s < nseg; ++s) {
+    m.sa[s] = StragArgs{nullptr, nullptr, 0u, 0, nullptr};
+    const int b = m.seg[s].bucket;
+    if (!handoff || (b != 3 && b != 13) || segs[s].n_cells == 0) continue;
+    const int64_t cap = mixed_rec_cap(segs[s].n_cells);
+    m.sa[s] = StragArgs{rec + off, rcnt + 4 * s, (uint32_t)cap, MIXED_STRAG_STEPS, nullptr};
+    off += (b == 3) ? rec_bytes<3, LT>(cap) : rec_bytes<13, LT>(cap);
+  }
+  k_burn_mixed<LT><<<(unsigned)blocks, 128, msmem, st>>>(m, o, next);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "mixed launch");
+  count_launch(1);
+  for (int s = 0; s < nseg; ++s) {
+    if (!m.sa[s].rec) continue;
+    const SegDev &g = m.seg[s];
+    mc_status r = (g.bucket == 3)
+                      ? launch_records<3, LT>(g.net, o, g.a, m.sa[s], next + MIXED_MAX_SEGS + s, sms, st)
+                      : launch_records<13, LT>(g.net, o, g.a, m.sa[s], next + MIXED_MAX_SEGS + s, sms, st);
+    if (r != MC_OK) return r;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "mixed record pass");
+  return MC_OK;
+}
+
+// Queue resets and kernels of one mixed burn on stream st (capturable once
+// mixed_reserve has sized the scratch).
+mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts &ob, double dt,
+                       cudaStream_t st) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  mc_status rs = mixed_reserve(segs, nseg, ob, st);
+  if (rs != MC_OK) return rs;
+  int64_t total = 0;
+  for (int s = 0; s < nseg; ++s) total += segs[s].n_cells;
+  unsigned long long *next;
+  uint32_t *rcount;
+  int32_t *retry;
+  scratch_stream(st);
+  rs = scratch_get(dev, ob.lu_precision == 32 ? total : 0, &next, &rcount, &retry);
+  if (rs != MC_OK) return rs;
+  int32_t *order;
+  uint8_t *bkt;
+  uint32_t *hist;
+  rs = order_scratch(dev, std::max<int64_t>(1, total), &order, &bkt, &hist);
+  if (rs != MC_OK) return rs;
+  void *rec = nullptr;
+  uint32_t *rcnt = nullptr;
+  const size_t rb = mixed_rec_total(segs, nseg, ob.lu_precision);
+  if (rb > 0) {
+    rs = straggler_scratch(rb, &rec, &rcnt);
+    if (rs != MC_OK) return rs;
+  }
+  const Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps, ob.jacobian == MC_JAC_FD ? 1 : 0};
   MixedArgs m{};
   m.nseg = nseg;
   int64_t off = 0;
-  int nmax = 0;
   for (int s = 0; s < nseg; ++s) {
     const mc_segment &g = segs[s];
     SegDev &d = m.seg[s];
     d.net = dnet_of(g.net);
     d.bucket = bucket_of(g.net->n);
-    nmax = std::max(nmax, g.net->n);
     CellArgs &a = d.a;
     a = CellArgs{};
     a.n_cells = g.n_cells;
     a.ld = g.ld;
-    a.dt = dt;
+    a.dt = g.dt > 0.0 ? g.dt : dt;
     a.x = g.x;
     a.T = g.T;
     a.nd = g.ndens;
     a.ks = g.rate_scale;
     a.status = g.status;
     a.stats = g.stats;
+    // each segment's queue hands out its cells in decreasing cost order
+    if (g.n_cells > 0) {
+      rs = order_cells(g.net, o, a, order + off, bkt + off, hist, st);
+      if (rs != MC_OK) return rs;
+      a.index = order + off;
+    }
     if (ob.lu_precision == 32) {
       a.retry = retry + off;
       a.retry_count = rcount + s;
-      off += g.n_cells;
+      a.retry_mask = FP32_RETRY_MASK;
     }
+    off += g.n_cells;
   }
   Tuned tu = autotune_pick(nullptr, ob);
-  const Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps};
-  // shared workspace of the warp-per-cell segments (the largest one)
+  // warp workspace (the largest one): the warp-per-cell segments' state, the
+  // thread-per-cell segments' cooperative matrix work
   size_t per_warp = 16;
   for (int s = 0; s < nseg; ++s) {
     const int b = m.seg[s].bucket, R = segs[s].net->R;
-    if (b == 33) per_warp = std::max(per_warp, ob.lu_precision == 64 ? wsh_bytes<33, double>(R) : wsh_bytes<33, float>(R));
-    if (b == 40) per_warp = std::max(per_warp, ob.lu_precision == 64 ? wsh_bytes<40, double>(R) : wsh_bytes<40, float>(R));
+    const bool f = ob.lu_precision == 32;
+    if (b == 3) per_warp = std::max(per_warp, f ? wsh_bytes<3, float>(R) : wsh_bytes<3, double>(R));
+    if (b == 13) per_warp = std::max(per_warp, f ? wsh_bytes<13, float>(R) : wsh_bytes<13, double>(R));
+    if (b == 33) per_warp = std::max(per_warp, f ? wsh_bytes<33, float>(R) : wsh_bytes<33, double>(R));
+    if (b == 40) per_warp = std::max(per_warp, f ? wsh_bytes<40, float>(R) : wsh_bytes<40, double>(R));
+  }
+  // the FP64 retry pass runs on the same workspace size (its matrices are
+  // larger than the FP32 pass's)
+  for (int s = 0; s < nseg; ++s) {
+    const int b = m.seg[s].bucket, R = segs[s].net->R;
+    if (b == 3) per_warp = std::max(per_warp, wsh_bytes<3, double>(R));
+    if (b == 13) per_warp = std::max(per_warp, wsh_bytes<13, double>(R));
+    if (b == 33) per_warp = std::max(per_warp, wsh_bytes<33, double>(R));
+    if (b == 40) per_warp = std::max(per_warp, wsh_bytes<40, double>(R));
   }
   m.smem_per_warp = (int)per_warp;
   const int mthreads = 128;
   const int msmem = (int)per_warp * (mthreads / 32);
   {
-    // both precisions run in one call (FP32 pass, FP64 retry pass)
     static thread_local DevAttrCache configured;
     if (configured.below(dev, msmem)) {
       cudaError_t ea = cudaFuncSetAttribute(k_burn_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem);
@@ -109,37 +252,28 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
       configured.raise(dev, msmem);
     }
   }
-  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long) * nseg, st);
-  if (e == cudaSuccess && ob.lu_precision == 32) e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t) * nseg, st);
-  if (e != cudaSuccess) return cuda_error(e, "mixed queue reset");
-  const unsigned blocks = (unsigned)std::max(1, sms * tu.blocks_per_sm);
-  if (ob.lu_precision == 64) {
-    k_burn_mixed<double><<<blocks, mthreads, msmem, st>>>(m, o, next);
-  } else {
-    k_burn_mixed<float><<<blocks, mthreads, msmem, st>>>(m, o, next);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "mixed launch");
-    count_launch(1);
-    // FP64 pass over every segment's retry list (lengths read on the device)
-    MixedArgs r = m;
-    off = 0;
-    for (int s = 0; s < nseg; ++s) {
-      CellArgs &a = r.seg[s].a;
-      a.index = retry + off;
-      a.n_dev = rcount + s;
-      a.retry = nullptr;
-      a.retry_count = nullptr;
-      off += segs[s].n_cells;
-    }
-    e = cudaMemsetAsync(next, 0, sizeof(unsigned long long) * nseg, st);
-    if (e != cudaSuccess) return cuda_error(e, "mixed queue reset");
-    k_burn_mixed<double><<<blocks, mthreads, msmem, st>>>(r, o, next);
+  if (ob.lu_precision == 32) {
+    cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t) * nseg, st);
+    if (e != cudaSuccess) return cuda_error(e, "mixed retry reset");
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_error(e, "mixed launch");
-  count_launch(1);
-  (void)nmax;
-  return MC_OK;
+  const int blocks = std::max(1, sms * tu.blocks_per_sm);
+  const bool handoff = tu.strag_steps >= 0;
+  if (ob.lu_precision == 64)
+    return mixed_pass<double>(segs, m, o, blocks, msmem, handoff, next, rcnt, (char *)rec, sms, st);
+  rs = mixed_pass<float>(segs, m, o, blocks, msmem, handoff, next, rcnt, (char *)rec, sms, st);
+  if (rs != MC_OK) return rs;
+  // FP64 pass over every segment's retry list (lengths read on the device), no hand-off
+  MixedArgs r = m;
+  off = 0;
+  for (int s = 0; s < nseg; ++s) {
+    CellArgs &a = r.seg[s].a;
+    a.index = retry + off;
+    a.n_dev = rcount + s;
+    a.retry = nullptr;
+    a.retry_count = nullptr;
+    off += segs[s].n_cells;
+  }
+  return mixed_pass<double>(segs, r, o, blocks, msmem, false, next, rcnt, (char *)rec, sms, st);
 }
 
 }  // namespace
@@ -191,6 +325,7 @@ extern "C" mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, con
   // the graph keeps the scratch set of its capture stream (allocated here, before capture)
   scratch_stream(cs);
   s = scratch_get(dev, o.lu_precision == 32 ? total : 0, &next, &rcount, &retry);
+  if (s == MC_OK) s = mixed_reserve(segs, n_segs, o, cs);
   if (s != MC_OK) {
     cudaStreamDestroy(cs);
     return s;

@@ -18,7 +18,9 @@ using namespace mc;
 namespace {
 
 constexpr size_t kHead = 256;  // queue counters (2 x 8 bytes) at 0, retry count at 128
-// Every GPU that loads the library holds this array until the process exits.
+// Part of this file's device code: CUDA allocates it on a device when it
+// loads that code there (lazily, at the first call's address look-up below),
+// and it stays until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kHead + sizeof(int32_t) * MC_NOALLOC_MAX_CELLS];
 
 std::mutex g_mu;

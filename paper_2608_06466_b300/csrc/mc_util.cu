@@ -22,7 +22,7 @@ mc_status rate(int iters, int blocks_per_sm, double *tflops) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int threads = 128, blocks = sms * blocks_per_sm;
   T *buf = nullptr;
-  cudaError_t e = cudaMalloc(&buf, sizeof(T) * (size_t)blocks * threads);
+  cudaError_t e = mc::dev_malloc((void **)&buf, sizeof(T) * (size_t)blocks * threads);
   if (e != cudaSuccess) return mc::cuda_error(e, "probe allocation");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

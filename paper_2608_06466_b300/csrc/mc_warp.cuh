@@ -17,54 +17,10 @@
 
 namespace mc {
 
-constexpr unsigned WFULL = 0xffffffffu;
-
-__device__ __forceinline__ double wsum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(WFULL, v, o);
-  return v;
-}
-
-// per-warp shared workspace (carved from dynamic shared memory)
-template <typename LT>
-struct WSh {
-  LT *J;            // [N*N] Jacobian, row stride N
-  LT *P;            // [N*N] factored iteration matrix
-  unsigned char *piv;
-  double *yb;       // [N]   point of the right-hand side, for broadcast
-  double *wb;       // [R]   net reaction rates
-  double *dw;       // [5R]  d w / d x per side slot, then d w / d T
-};
-
-template <int N, typename LT>
-__host__ __device__ inline size_t wsh_bytes(int R) {
-  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  return al(sizeof(LT) * N * N) * 2 + al(N) + al(sizeof(double) * N) + al(sizeof(double) * (R > 0 ? R : 1)) +
-         al(sizeof(double) * 5 * (R > 0 ? R : 1));
-}
-
-template <int N, typename LT>
-__device__ __forceinline__ WSh<LT> wsh_carve(unsigned char *p, int R) {
-  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  WSh<LT> s;
-  s.J = (LT *)p;
-  p += al(sizeof(LT) * N * N);
-  s.P = (LT *)p;
-  p += al(sizeof(LT) * N * N);
-  s.piv = p;
-  p += al(N);
-  s.yb = (double *)p;
-  p += al(sizeof(double) * N);
-  s.wb = (double *)p;
-  p += al(sizeof(double) * (R > 0 ? R : 1));
-  s.dw = (double *)p;
-  return s;
-}
-
 // register state of the warp's cell (vector slots: component lane + 32 s)
 template <int N>
 struct WState {
-  static constexpr int NS = (N + 31) / 32;
+  static constexpr int NS = WSlots<N>::NS;
   double z[QMAX + 2][NS];
   double e[NS], es[NS], iw[NS], y[NS], f[NS];
   double l[QMAX + 1];
@@ -76,8 +32,6 @@ struct WState {
   bool need_j, need_p, jcur, have_es, last;
   int st[NSTAT];
 };
-
-__device__ __forceinline__ int wlane() { return threadIdx.x & 31; }
 
 // value of distributed component c (all lanes receive it)
 template <int NS>
@@ -110,7 +64,8 @@ __device__ __forceinline__ void w_load(WState<N> &W, const Lane<N, LT> &L, const
   for (int k = 0; k < NS; ++k) {
     const int i = ln + 32 * k;
     const bool in = i < n;
-    for (int j = 0; j < QMAX + 2; ++j) W.z[j][k] = in ? L.z[j][in ? i : 0] : 0.0;
+    for (int j = 0; j < QMAX + 1; ++j) W.z[j][k] = in ? L.z[j][in ? i : 0] : 0.0;
+    W.z[QMAX + 1][k] = 0.0;
     W.e[k] = in ? L.e[in ? i : 0] : 0.0;
     W.es[k] = in ? L.es[in ? i : 0] : 0.0;
     W.iw[k] = in ? L.iw[in ? i : 0] : 0.0;
@@ -169,6 +124,7 @@ __device__ __forceinline__ void w_load_cell(WState<N> &W, const DNet &net, const
   W.cin.nd = nd;
   W.cin.ks = a.ks ? a.ks + c : nullptr;
   W.cin.ks_ld = a.ld;
+  W.cin.src = a.src ? a.src + c : nullptr;
   if (net.energy) {
     if (!(X > 0.0) || !isfinite(X)) good = false;
     const double u = X * KB_EV * T / net.gm1;
@@ -194,205 +150,28 @@ __device__ __forceinline__ void w_load_cell(WState<N> &W, const DNet &net, const
   W.phase = PH_F0;
 }
 
-// temperature quantities of the point in sh.yb (energy form) or of the cell
-__device__ __forceinline__ bool w_temperature(const DNet &net, const CellIn &c, const double *yb, double &T,
-                                              double &X, double &lnT, double &invT) {
-  lnT = c.lnT;
-  invT = c.invT;
-  T = 0.0;
-  X = 0.0;
-  if (!net.energy) return true;
-  double xs = 0.0;
-  for (int i = wlane(); i < net.S; i += 32) xs += yb[i];
-  X = wsum(xs);
-  T = net.gm1 * yb[net.S] / (KB_EV * X);
-  if (!(T > 0.0) || !isfinite(T)) return false;
-  lnT = log(T);
-  invT = 1.0 / T;
-  return true;
-}
-
 // Right-hand side at W.y into W.f; returns false (uniformly) when it cannot be evaluated.
 template <int N, typename LT>
 __device__ __forceinline__ bool w_rhs(WState<N> &W, const WSh<LT> &sh, const DNet &net) {
   constexpr int NS = WState<N>::NS;
-  const int n = net.n, S = net.S, ln = wlane();
+  const int n = net.n, ln = wlane();
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     const int i = ln + 32 * k;
     if (i < n) sh.yb[i] = W.y[k];
   }
   __syncwarp();
-  double T, X, lnT, invT;
-  if (!w_temperature(net, W.cin, sh.yb, T, X, lnT, invT)) return false;
-  const CellIn &c = W.cin;
-  double epart = 0.0;
-  for (int r = ln; r < net.R; r += 32) {
-    const int4 s = __ldg(&net.side[r]);
-    const RxPar &p = net.par[r];
-    double kf = rexp(__ldg(&p.lnAf) + __ldg(&p.bf) * lnT - __ldg(&p.Cf) * invT, net.exptab);
-    double kr = 0.0;
-    if (__ldg(&p.rev) != 0.0) kr = rexp(__ldg(&p.lnAr) + __ldg(&p.br) * lnT - __ldg(&p.Cr) * invT, net.exptab);
-    if (c.ks) {
-      const double sc = c.ks[r * c.ks_ld];
-      kf *= sc;
-      kr *= sc;
-    }
-    const double pf = (s.y < 0) ? sh.yb[s.x] : c.nd * sh.yb[s.x] * sh.yb[s.y];
-    const double pr = (s.w < 0) ? sh.yb[s.z] : c.nd * sh.yb[s.z] * sh.yb[s.w];
-    const double w = kf * pf - kr * pr;
-    sh.wb[r] = w;
-    if (net.energy) epart += __ldg(&p.dE) * w;
-  }
-  __syncwarp();
-  const double fu = net.energy ? wsum(epart) : 0.0;
-  bool bad = false;
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    const int i = ln + 32 * k;
-    double v = 0.0;
-    if (i < S) {
-      for (int q = __ldg(&net.csr_ptr[i]); q < __ldg(&net.csr_ptr[i + 1]); ++q) {
-        const int ent = __ldg(&net.csr_ent[q]);
-        const double w = sh.wb[ent >> 2];
-        v = ((ent & 3) < 2) ? v - w : v + w;
-      }
-    } else if (i == S && net.energy) {
-      v = fu;
-    }
-    W.f[k] = v;
-    if (i < n && !isfinite(v)) bad = true;
-  }
-  __syncwarp();
-  return !__any_sync(WFULL, bad);
+  return w_rhs_core<N, LT>(net, W.cin, sh, W.f);
 }
 
-// Analytic Jacobian at the point in sh.yb, into sh.J (same formulas as net_jac).
+// x = (LU)^-1 b for the distributed vector b (FP64 in), in precision LT.
 template <int N, typename LT>
-__device__ __forceinline__ bool w_jac(WState<N> &W, const WSh<LT> &sh, const DNet &net) {
-  const int n = net.n, S = net.S, ln = wlane();
-  double T, X, lnT, invT;
-  if (!w_temperature(net, W.cin, sh.yb, T, X, lnT, invT)) return false;
-  const CellIn &c = W.cin;
-  double gpart = 0.0;
-  for (int r = ln; r < net.R; r += 32) {
-    const int4 s = __ldg(&net.side[r]);
-    const RxPar &p = net.par[r];
-    const double bf = __ldg(&p.bf), Cf = __ldg(&p.Cf);
-    double kf = rexp(__ldg(&p.lnAf) + bf * lnT - Cf * invT, net.exptab);
-    double kr = 0.0, br = 0.0, Cr = 0.0;
-    if (__ldg(&p.rev) != 0.0) {
-      br = __ldg(&p.br);
-      Cr = __ldg(&p.Cr);
-      kr = rexp(__ldg(&p.lnAr) + br * lnT - Cr * invT, net.exptab);
-    }
-    if (c.ks) {
-      const double sc = c.ks[r * c.ks_ld];
-      kf *= sc;
-      kr *= sc;
-    }
-    double *d = sh.dw + 5 * r;
-    double pf, pr;
-    if (s.y < 0) { pf = sh.yb[s.x]; d[0] = kf; d[1] = 0.0; }
-    else { pf = c.nd * sh.yb[s.x] * sh.yb[s.y]; d[0] = kf * (c.nd * sh.yb[s.y]); d[1] = kf * (c.nd * sh.yb[s.x]); }
-    if (s.w < 0) { pr = sh.yb[s.z]; d[2] = -kr; d[3] = 0.0; }
-    else { pr = c.nd * sh.yb[s.z] * sh.yb[s.w]; d[2] = -kr * (c.nd * sh.yb[s.w]); d[3] = -kr * (c.nd * sh.yb[s.z]); }
-    d[4] = kf * (bf + Cf * invT) * invT * pf - kr * (br + Cr * invT) * invT * pr;
-    if (net.energy) gpart += __ldg(&p.dE) * d[4];
-  }
-  __syncwarp();
-  const double gS = net.energy ? wsum(gpart) : 0.0;
-  for (int idx = ln; idx < n * N; idx += 32) sh.J[idx] = (LT)0;
-  __syncwarp();
-  bool bad = false;
-  // species rows: lane i assembles row i from the reactions species i takes part in
-  for (int i = ln; i < n; i += 32) {
-    double g = 0.0;
-    if (i < S) {
-      for (int q = __ldg(&net.csr_ptr[i]); q < __ldg(&net.csr_ptr[i + 1]); ++q) {
-        const int ent = __ldg(&net.csr_ent[q]);
-        const int r = ent >> 2;
-        const double sgn = ((ent & 3) < 2) ? -1.0 : 1.0;
-        const int4 s = __ldg(&net.side[r]);
-        const int col[4] = {s.x, s.y, s.z, s.w};
-        const double *d = sh.dw + 5 * r;
-        g += sgn * d[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (col[b] >= 0) sh.J[i * N + col[b]] += (LT)(sgn * d[b]);
-      }
-    } else {
-      g = gS;
-    }
-    if (net.energy) {
-      const double dTdx = -T / X, dTdu = net.gm1 / (KB_EV * X);
-      if (i == S) {
-        // energy row: column j collects dE_r d w_r / d x_j over species j's slots
-        for (int j = 0; j < S; ++j) {
-          double acc = 0.0;
-          for (int q = __ldg(&net.csr_ptr[j]); q < __ldg(&net.csr_ptr[j + 1]); ++q) {
-            const int ent = __ldg(&net.csr_ent[q]);
-            acc += __ldg(&net.par[ent >> 2].dE) * sh.dw[5 * (ent >> 2) + (ent & 3)];
-          }
-          sh.J[S * N + j] += (LT)acc;
-        }
-      }
-      const LT gx = (LT)(g * dTdx);
-      for (int j = 0; j < S; ++j) sh.J[i * N + j] += gx;
-      sh.J[i * N + S] += (LT)(g * dTdu);
-    }
-    for (int j = 0; j < n; ++j)
-      if (!isfinite((double)sh.J[i * N + j])) bad = true;
-  }
-  __syncwarp();
-  return !__any_sync(WFULL, bad);
-}
-
-// Row-parallel LU with partial pivoting in shared memory (first maximal |a|).
-template <int N, typename LT>
-__device__ __forceinline__ bool w_lu(const WSh<LT> &sh, int n) {
-  const int ln = wlane();
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = n;
-    for (int i = k + ln; i < n; i += 32) {
-      const double v = fabs((double)sh.P[i * N + k]);
-      if (v > best) { best = v; bi = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(WFULL, best, o);
-      const int oi = __shfl_xor_sync(WFULL, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if (ln == 0) sh.piv[k] = (unsigned char)bi;
-    if (!(best > 0.0)) { __syncwarp(); return false; }
-    if (bi != k)
-      for (int j = ln; j < n; j += 32) {
-        const LT tmp = sh.P[k * N + j];
-        sh.P[k * N + j] = sh.P[bi * N + j];
-        sh.P[bi * N + j] = tmp;
-      }
-    __syncwarp();
-    const LT inv = (LT)1 / sh.P[k * N + k];
-    for (int i = k + 1 + ln; i < n; i += 32) {
-      const LT m = sh.P[i * N + k] * inv;
-      sh.P[i * N + k] = m;
-      for (int j = k + 1; j < n; ++j) sh.P[i * N + j] -= m * sh.P[k * N + j];
-    }
-    __syncwarp();
-  }
-  return true;
-}
-
-// Solve (LU) x = P d for the distributed vector d (in place), in precision LT.
-template <int N, typename LT>
-__device__ __forceinline__ void w_solve(const WSh<LT> &sh, int n, double (&d)[WState<N>::NS]) {
+__device__ __forceinline__ void w_apply(const WSh<LT> &sh, int n, const double (&bd)[WState<N>::NS],
+                                        LT (&b)[WState<N>::NS]) {
   constexpr int NS = WState<N>::NS;
   const int ln = wlane();
-  LT b[NS];
 #pragma unroll
-  for (int k = 0; k < NS; ++k) b[k] = (LT)d[k];
+  for (int k = 0; k < NS; ++k) b[k] = (LT)bd[k];
   auto get = [&](int c) -> LT {
     LT x = b[0];
     if (NS > 1 && c >= 32) x = b[NS - 1];
@@ -422,7 +201,7 @@ __device__ __forceinline__ void w_solve(const WSh<LT> &sh, int n, double (&d)[WS
   }
   for (int j = n - 1; j >= 0; --j) {
     LT bj = get(j);
-    bj = bj / sh.P[j * N + j];
+    bj = bj * sh.P[j * N + j];
     put(j, bj);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
@@ -430,8 +209,72 @@ __device__ __forceinline__ void w_solve(const WSh<LT> &sh, int n, double (&d)[WS
       if (i < j) b[k] -= sh.P[i * N + j] * bj;
     }
   }
+}
+
+// Newton correction d <- (I - gamma_P J)^-1 d for the distributed d: the
+// thread form's newton_solve (FP64 factors: one solve; FP32 factors: the same
+// mixed-precision iterative refinement, rows of J on their lanes). Returns
+// false (uniformly) when the refinement cannot reach the FP64 solve.
+template <int N, typename LT>
+__device__ __forceinline__ bool w_solve(const WSh<LT> &sh, int n, double gamma_p, const double (&iw)[WState<N>::NS],
+                                        double (&d)[WState<N>::NS]) {
+  constexpr int NS = WState<N>::NS;
+  const int ln = wlane();
+  LT b[NS];
+  if constexpr (sizeof(LT) == sizeof(double)) {
+    w_apply<N, LT>(sh, n, d, b);
 #pragma unroll
-  for (int k = 0; k < NS; ++k) d[k] = (double)b[k];
+    for (int k = 0; k < NS; ++k) d[k] = (double)b[k];
+    return true;
+  } else {
+    double r[NS];
+    float w[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      r[k] = d[k];
+      w[k] = (float)iw[k];
+    }
+    w_apply<N, LT>(sh, n, r, b);
+    float nl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      d[k] = (ln + 32 * k < n) ? (double)b[k] : 0.0;
+      if (ln + 32 * k < n) nl = fmaxf(nl, fabsf(b[k]) * w[k]);
+    }
+    const float nd = wmaxf(nl);
+    float np = nd;
+    for (int it = 0; it < REFINE_MAX; ++it) {
+      double acc[NS], s[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) acc[k] = 0.0;
+      for (int j = 0; j < n; ++j) {
+        double x = d[0];
+        if (NS > 1 && j >= 32) x = d[NS - 1];
+        const double dj = __shfl_sync(WFULL, x, j & 31);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          const int i = ln + 32 * k;
+          if (i < n) acc[k] = fma(sh.J[i * N + j], dj, acc[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NS; ++k) s[k] = (ln + 32 * k < n) ? fma(gamma_p, acc[k], r[k] - d[k]) : 0.0;
+      w_apply<N, LT>(sh, n, s, b);
+      nl = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        if (ln + 32 * k < n) nl = fmaxf(nl, fabsf(b[k]) * w[k]);
+      const float nc = wmaxf(nl);
+      const bool done = nc <= REFINE_TOL * nd;
+      if (!done && !(nc < np)) return false;  // no longer contracting
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        if (ln + 32 * k < n) d[k] += (double)b[k];
+      if (done || nc * (nc / np) <= REFINE_TOL * nd) return true;
+      np = nc;
+    }
+    return false;
+  }
 }
 
 // ---- step logic (mirrors the thread form in mc_device.cuh) -----------------
@@ -583,7 +426,7 @@ __device__ __forceinline__ void w_after_convergence(WState<N> &W, const DNet &ne
       W.phase = PH_RESTART;
       return;
     }
-    double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
+    double eta = 1.0 / (root_k(BIAS_Q * dsm, q + 1, net.exptab) + ADDON);
     int qn = q;
     if (q > 1) {
       xi_of(W.h, W.hist, q, xi);
@@ -603,7 +446,7 @@ __device__ __forceinline__ void w_after_convergence(WState<N> &W, const DNet &ne
 #pragma unroll
           for (int k = 0; k < NS; ++k) zq[k] = W.z[j][k];
       const double est = (prod / l1) * w_wrms<N>(n, zq, W.iw);
-      const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
+      const double eta_m = 1.0 / (root_k(BIAS_QM1 * est, q, net.exptab) + ADDON);
       if (eta_m > eta) { eta = eta_m; qn = q - 1; }
     }
     eta = fmax(ETAMIN, fmin(eta, 1.0));
@@ -637,7 +480,7 @@ __device__ __forceinline__ void w_after_convergence(WState<N> &W, const DNet &ne
   }
   if (W.last) { W.status = CELL_OK; W.phase = PH_DONE; return; }
   if (W.qwait > 0) { w_begin_step(W, net, o); return; }
-  double eta = 1.0 / (pow(BIAS_Q * dsm, 1.0 / (q + 1)) + ADDON);
+  double eta = 1.0 / (root_k(BIAS_Q * dsm, q + 1, net.exptab) + ADDON);
   int qn = q;
   xi_of(W.h, W.hist, q + 1, xi);
   if (q > 1) {
@@ -657,16 +500,16 @@ __device__ __forceinline__ void w_after_convergence(WState<N> &W, const DNet &ne
 #pragma unroll
         for (int k = 0; k < NS; ++k) zq[k] = W.z[j][k];
     const double est = (prod / l1) * w_wrms<N>(n, zq, W.iw);
-    const double eta_m = 1.0 / (pow(BIAS_QM1 * est, 1.0 / q) + ADDON);
+    const double eta_m = 1.0 / (root_k(BIAS_QM1 * est, q, net.exptab) + ADDON);
     if (eta_m > eta) { eta = eta_m; qn = q - 1; }
   }
   if (q < o.qmax && W.have_es) {
-    const double r = pow(W.h / W.esave_h, (double)(q + 1));
+    const double r = ipow(W.h / W.esave_h, q + 1);
     double dv[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) dv[s] = W.e[s] - r * W.es[s];
     const double est = w_wrms<N>(n, dv, W.iw) / ((double)(q + 2) * harmonic(q + 1));
-    const double eta_p = 1.0 / (pow(BIAS_QP1 * est, 1.0 / (q + 2)) + ADDON);
+    const double eta_p = 1.0 / (root_k(BIAS_QP1 * est, q + 2, net.exptab) + ADDON);
     if (eta_p > eta) { eta = eta_p; qn = q + 1; }
   }
   W.have_es = false;
@@ -705,7 +548,8 @@ __device__ __forceinline__ void w_after_convergence(WState<N> &W, const DNet &ne
 }
 
 template <int N, typename LT>
-__device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, const DNet &net, bool ok) {
+__device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, const DNet &net, const Opts &o,
+                                             bool ok) {
   constexpr int NS = WState<N>::NS;
   const int n = net.n, ln = wlane();
   if (!ok) return 3;
@@ -713,7 +557,7 @@ __device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, co
   if (W.m == 0) {
     bool newp = false;
     if (W.need_j || W.jage >= MSBJ) {
-      if (!w_jac<N, LT>(W, sh, net)) return 3;
+      if (!(o.jac_fd ? w_fd_jac<N, LT>(net, W.cin, sh, o.rtol, o.atol) : w_jac<N, LT>(net, W.cin, sh))) return 3;
       W.st[ST_JAC] += 1;
       W.jcur = true;
       W.need_j = false;
@@ -721,12 +565,7 @@ __device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, co
       newp = true;
     }
     if (newp || W.need_p || W.page >= MSBP || fabs(W.gamma / W.gamma_p - 1.0) > CCMAX) {
-      const LT g = (LT)W.gamma;
-      for (int idx = ln; idx < n * N; idx += 32) {
-        const int i = idx / N, j = idx - i * N;
-        if (j < n) sh.P[idx] = (i == j ? (LT)1 : (LT)0) - g * sh.J[idx];
-      }
-      __syncwarp();
+      w_form_p<N, LT>(sh, n, W.gamma);
       W.st[ST_LU] += 1;
       W.gamma_p = W.gamma;
       W.page = 0;
@@ -739,13 +578,13 @@ __device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, co
     }
   }
   double d[NS];
-  const double rl1 = W.l[1];
+  const double rl1 = 1.0 / W.l[1];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const int i = ln + 32 * s;
-    d[s] = (i < n) ? (W.h * W.f[s] - W.z[1][s]) / rl1 - W.e[s] : 0.0;
+    d[s] = (i < n) ? (W.h * W.f[s] - W.z[1][s]) * rl1 - W.e[s] : 0.0;
   }
-  w_solve<N, LT>(sh, n, d);
+  if (!w_solve<N, LT>(sh, n, W.gamma_p, W.iw, d)) return 4;
   W.st[ST_NEWTON] += 1;
   if (W.gamma != W.gamma_p) {
     const double sc = 2.0 / (1.0 + W.gamma / W.gamma_p);
@@ -827,8 +666,9 @@ __device__ __forceinline__ void w_advance(WState<N> &W, const WSh<LT> &sh, const
     return;
   }
   if (W.phase == PH_NEWTON) {
-    const int r = w_newton_iter<N, LT>(W, sh, net, ok);
+    const int r = w_newton_iter<N, LT>(W, sh, net, o, ok);
     if (r == 0) return;
+    if (r == 4) { W.status = CELL_RETRY64; W.phase = PH_DONE; return; }  // to the FP64 retry pass
     if (r == 1) { w_after_convergence(W, net, o); return; }
     if (r == 2 && !W.jcur) {
       W.need_j = true;
@@ -861,14 +701,16 @@ __device__ __forceinline__ void w_store(WState<N> &W, const DNet &net, const Cel
   constexpr int NS = WState<N>::NS;
   const int64_t c = W.cell;
   const int S = net.S, ln = wlane();
-  if (a.retry && (W.status == CELL_CONV_FAIL || W.status == CELL_H_UNDERFLOW)) {
+  const int route = route_of(a, W.status);
+  if (route != 0) {
     if (ln == 0) {
-      const uint32_t k = atomicAdd(a.retry_count, 1u);
-      a.retry[k] = (int32_t)c;
+      if (route == 1) push_list(a.retry, a.retry_count, c);
+      else push_list(a.lretry, a.lretry_count, c);
     }
     __syncwarp();
     return;
   }
+  if (a.rung && ln == 0) a.rung[c] = a.rung_id;
   if (!(W.status == CELL_BAD_INPUT && W.m < 0)) {
     double xs = 0.0;
 #pragma unroll
@@ -935,26 +777,28 @@ constexpr int MIXED_MAX_SEGS = 8;
 
 struct MixedArgs {
   SegDev seg[MIXED_MAX_SEGS];
+  StragArgs sa[MIXED_MAX_SEGS];  // hand-off of the thread-per-cell segments (rec = nullptr: none)
   int nseg;
-  int smem_per_warp;  // shared workspace of the warp-per-cell segments
+  int smem_per_warp;  // warp workspace (the largest segment's)
 };
 
 // Mixed persistent launch: every warp drains the segment queues starting at a
 // segment chosen by its warp index, so all networks start at once and warps
 // that finish one network move on to the next (one launch for all networks).
-// Networks of up to 13 ODEs run thread-per-cell, larger ones warp-per-cell.
+// Networks of up to 13 ODEs run thread-per-cell (a cell still running after
+// the hand-off threshold goes to its segment's record list, finished after the
+// launch by k_burn_straggler), larger ones warp-per-cell.
 template <typename LT>
 __global__ void __launch_bounds__(128) k_burn_mixed(MixedArgs m, Opts o, unsigned long long *next) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char *wsp = smem + (threadIdx.x >> 5) * (size_t)m.smem_per_warp;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const StragArgs sa{nullptr, nullptr, 0u, 0};
   for (int s0 = 0; s0 < m.nseg; ++s0) {
     const int s = (s0 + warp) % m.nseg;
     const SegDev &g = m.seg[s];
     switch (g.bucket) {
-      case 3: persistent_worker<3, LT>(g.net, o, g.a, next + s, sa); break;
-      case 13: persistent_worker<13, LT>(g.net, o, g.a, next + s, sa); break;
+      case 3: persistent_worker<3, LT>(g.net, o, g.a, next + s, m.sa[s], wsh_carve<3, LT>(wsp, g.net.R)); break;
+      case 13: persistent_worker<13, LT>(g.net, o, g.a, next + s, m.sa[s], wsh_carve<13, LT>(wsp, g.net.R)); break;
       case 33: warp_worker<33, LT>(g.net, o, g.a, next + s, wsh_carve<33, LT>(wsp, g.net.R)); break;
       default: warp_worker<40, LT>(g.net, o, g.a, next + s, wsh_carve<40, LT>(wsp, g.net.R)); break;
     }
@@ -1070,13 +914,13 @@ template <int N, typename LT>
 __global__ void __launch_bounds__(128, 3) k_burn_fused(DNet net, Opts o, CellArgs a, unsigned long long *next,
                                                        StragArgs sa, FuseArgs fa, int smem_per_warp) {
   extern __shared__ __align__(16) unsigned char smem[];
-  persistent_worker<N, LT>(net, o, a, next, sa);
+  const WSh<LT> sh = wsh_carve<N, LT>(smem + (threadIdx.x >> 5) * (size_t)smem_per_warp, net.R);
+  persistent_worker<N, LT>(net, o, a, next, sa, sh);
   __syncwarp();
   if (wlane() == 0) {
     __threadfence();
     atomicAdd(fa.bulk_done, 1u);
   }
-  const WSh<LT> sh = wsh_carve<N, LT>(smem + (threadIdx.x >> 5) * (size_t)smem_per_warp, net.R);
   fused_records<N, LT>(net, o, a, sa, fa, next, sh);
 }
 

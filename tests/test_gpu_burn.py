@@ -28,14 +28,13 @@ def _oracle(net, cells, dt, **kw):
     return oracle.burn(oracle.OracleNetwork(net), cells, dt, **kw)
 
 
-def _reference(net, cells, dt, index=None, lu=64):
-    """Oracle result, stability mask (perturbation matched to the matrix
-    precision under test) and tight-tolerance oracle result."""
+def _reference(net, cells, dt, index=None):
+    """Oracle result, stability mask, tight-tolerance oracle result and the
+    classification's re-probe (tests/parity.py)."""
     on = oracle.OracleNetwork(net)
-    (ox, oT, os_, ost), stable = classify(on, cells, dt, oracle.burn, index=index,
-                                          perturb=1e-13 if lu == 64 else 1e-9)
+    (ox, oT, os_, ost), stable, reprobe = classify(on, cells, dt, oracle.burn, index=index, with_reprobe=True)
     tx, tT, _, _ = oracle.burn(on, cells, dt, rtol=1e-10, atol=1e-16, index=index)
-    return ox, oT, os_, ost, stable, (tx, tT)
+    return ox, oT, os_, ost, stable, (tx, tT), reprobe
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])
@@ -45,7 +44,7 @@ def test_robertson_4096(mc, variant, lu):
     gx, gT, gs, gst = _run(mc, net, cells, 40.0, variant=variant, lu_precision=lu)
     ox, oT, os_, ost = _oracle(net, cells, 40.0)
     tx, _, _, _ = _oracle(net, cells, 40.0, rtol=1e-11, atol=1e-17)
-    rep = compare(gx, gT, gs, ox, oT, os_, ost, tight=(tx, None), fp32_matrix=(lu == 32))
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, tight=(tx, None))
     print(rep)
     assert rep["pass"], rep
     assert (gs == 0).all()
@@ -60,23 +59,27 @@ def test_synthetic_networks(mc, make, n, lu):
     net = make()
     cells = synthetic_cells(net, n, seed=3)
     gx, gT, gs, gst = _run(mc, net, cells, 1e10, lu_precision=lu)
-    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10, lu=lu)
-    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=(lu == 32))
+    ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, 1e10)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
     print(net.name, lu, rep, "same step count:", np.mean(gst[0] == ost[0]))
     assert rep["pass"], rep
     assert rep["stable"] >= 0.75 * n
 
 
-def test_full_size_sampled(mc):
-    """2^20 cells of the 13-ODE network in the default (benchmark) launch
-    configuration; 512 sampled cells recomputed by the oracle."""
+@pytest.mark.parametrize("lu,n_log2,variant", [(32, 22, 2), (64, 20, 1)])
+def test_full_size_sampled(mc, lu, n_log2, variant):
+    """The 13-ODE network at the workloads' full sizes in the launch
+    configurations the benchmark times: the FP32-matrix persistent path on
+    2^22 cells (its headline) and the plain FP64 path on 2^20 cells; 512
+    sampled cells recomputed by the oracle."""
     net = network_13()
-    cells = synthetic_cells(net, 1 << 20, seed=3)
-    gx, gT, gs, gst = _run(mc, net, cells, 1e10)
-    idx = np.sort(np.random.default_rng(0).choice(1 << 20, 512, replace=False))
-    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10, index=idx, lu=32)
-    rep = compare(gx[:, idx], gT[idx], gs[idx], ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=True)
-    print(rep)
+    n = 1 << n_log2
+    cells = synthetic_cells(net, n, seed=3)
+    gx, gT, gs, gst = _run(mc, net, cells, 1e10, lu_precision=lu, variant=variant)
+    idx = np.sort(np.random.default_rng(0).choice(n, 512, replace=False))
+    ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, 1e10, index=idx)
+    rep = compare(gx[:, idx], gT[idx], gs[idx], ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
+    print(lu, n, rep)
     assert rep["pass"], rep
     assert np.mean(gs == 0) > 0.99
 
@@ -88,8 +91,8 @@ def test_ragged_and_degenerate_sizes(mc, variant):
     for n in (1, 37, 129):
         cells = synthetic_cells(net, n, seed=11)
         gx, gT, gs, gst = mc.burn(h, cells, 1e10, mc.mc_burn_opts_default(variant=variant))
-        ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10)
-        rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight)
+        ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, 1e10)
+        rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
         assert rep["pass"], (n, rep)
     # zero cells is a no-op
     import torch
@@ -114,9 +117,9 @@ def test_leading_dimension_larger_than_count(mc):
     mc.mc_burn_batch(h, None, 100, 1e10, x, ld, T, nd, None, st, None)
     torch.cuda.synchronize()
     assert (x[:, 100:] == 7.0).all() and (T[100:] == 3.0).all() and (st[100:] == -9).all()
-    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10)
+    ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, 1e10)
     rep = compare(x[:, :100].cpu().numpy(), T[:100].cpu().numpy(), st[:100].cpu().numpy(), ox, oT, os_, ost,
-                  stable=stable, tight=tight)
+                  stable=stable, tight=tight, reprobe=rp)
     assert rep["pass"], rep
 
 
@@ -131,10 +134,10 @@ def test_bad_inputs_and_step_cap(mc):
     cells["ndens"][2] = 0.0
     cells["T"][3] = np.inf
     gx, gT, gs, gst = _run(mc, net, cells, 1e10)
-    ox, oT, os_, ost, stable, tight = _reference(net, cells, 1e10)
+    ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, 1e10)
     assert list(gs[:4]) == [4, 4, 4, 4] and list(os_[:4]) == [4, 4, 4, 4]
     np.testing.assert_array_equal(gT[1], -1.0)  # rejected cells are left untouched
-    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
     assert rep["pass"], rep
     # the step cap: same statuses and attempt counts. The states are compared
     # loosely: after 7 attempts they sit at slightly different times, because
@@ -191,8 +194,8 @@ def test_straggler_handoff_parity(mc, make, n, lu):
     else:
         cells, dt = synthetic_cells(net, n, seed=3), 1e10
     gx, gT, gs, gst = _run(mc, net, cells, dt, lu_precision=lu, variant=2, straggler_steps=40)
-    ox, oT, os_, ost, stable, tight = _reference(net, cells, dt, lu=lu)
-    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=(lu == 32))
+    ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, dt)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
     print(net.name, lu, rep, "handed off:", np.mean(ost[0] + ost[1] + ost[2] > 40))
     assert rep["pass"], rep
 
@@ -213,52 +216,79 @@ def test_fused_launch_matches_two_launches(mc):
         assert np.array_equal(u, v)
 
 
-def _segments(mc, batch):
-    import torch
+def _segments(mc, batch, dts):
     segs, keep = [], []
-    for net, cells, idx in batch["groups"]:
+    for (net, cells, idx), dt in zip(batch["groups"], dts):
         h = mc.Network(net)
         from paper_2608_06466_b300.api import to_device
         d = to_device(cells)
         keep.append((h, d, net, cells))
         n = cells["x"].shape[1]
-        segs.append(mc.segment(h, n, n, d["x"], d["T"], d["ndens"], d["rate_scale"], d["status"], d["stats"]))
+        segs.append(mc.segment(h, n, n, d["x"], d["T"], d["ndens"], d["rate_scale"], d["status"], d["stats"], dt=dt))
     return segs, keep
 
 
+def _snapshot(keep):
+    return [(d["x"].cpu().numpy().copy(), None if d["T"] is None else d["T"].cpu().numpy().copy(),
+             d["status"].cpu().numpy().copy(), d["stats"].cpu().numpy().copy()) for (_, d, _, _) in keep]
+
+
+def _reset(keep):
+    import torch
+    for (h, d, net, cells) in keep:
+        d["x"].copy_(torch.as_tensor(cells["x"]))
+        if d["T"] is not None:
+            d["T"].copy_(torch.as_tensor(cells["T"]))
+
+
+MIXED_DTS = [40.0, 1e10, 1e10]   # Robertson to t = 40, the energy networks over 1e10 s
+
+
 def test_mixed_batch_and_graph(mc):
+    """Robertson (3 ODEs, its own dt), net13 and net33 with 1 % hot cells in ONE
+    persistent launch; each segment against the oracle; a CUDA-graph replay of
+    the same launch reproduces it bit for bit, twice."""
     import torch
     from mc_inputs import mixed_batch
     batch = mixed_batch(3 * 700, seed=6, hot_fraction=0.01)
-    segs, keep = _segments(mc, batch)
-    dts = [40.0, 1e10, 1e10]
-    # networks differ in dt here only through the Robertson segment: run it separately
-    rob_seg, rob = segs[0], keep[0]
+    segs, keep = _segments(mc, batch, MIXED_DTS)
     opts = mc.mc_burn_opts_default(lu_precision=32)
-    mc.mc_burn_mixed(segs[1:], opts, 1e10)
-    mc.mc_burn_mixed([rob_seg], opts, 40.0)
+    mc.mc_burn_mixed(segs, opts, 1e10)
     torch.cuda.synchronize()
-    first = [(d["x"].cpu().numpy().copy(), None if d["T"] is None else d["T"].cpu().numpy().copy(),
-              d["status"].cpu().numpy().copy(), d["stats"].cpu().numpy().copy()) for (_, d, _, _) in keep]
-    for (h, d, net, cells), (gx, gT, gs, gst), dt in zip(keep, first, dts):
-        ox, oT, os_, ost, stable, tight = _reference(net, cells, dt, lu=32)
-        rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, fp32_matrix=True)
+    first = _snapshot(keep)
+    for (h, d, net, cells), (gx, gT, gs, gst), dt in zip(keep, first, MIXED_DTS):
+        ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, dt)
+        rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
         assert rep["pass"], (net.name, rep)
-    # graph replay of the energy segments reproduces the direct launch bitwise
     totals = torch.zeros(8, dtype=torch.int64, device="cuda")
-    g = mc.mc_graph_create(segs[1:], opts, 1e10, totals)
+    g = mc.mc_graph_create(segs, opts, 1e10, totals)
     for rep_i in range(2):
-        for (h, d, net, cells) in keep[1:]:
-            d["x"].copy_(torch.as_tensor(cells["x"]))
-            d["T"].copy_(torch.as_tensor(cells["T"]))
+        _reset(keep)
         g.launch()
         torch.cuda.synchronize()
-        for (h, d, net, cells), (gx, gT, gs, gst) in zip(keep[1:], first[1:]):
+        for (h, d, net, cells), (gx, gT, gs, gst) in zip(keep, first):
             np.testing.assert_array_equal(d["x"].cpu().numpy(), gx)
             np.testing.assert_array_equal(d["status"].cpu().numpy(), gs)
-        want = sum(d["stats"].cpu().numpy().astype(np.int64).sum(axis=1) for (_, d, _, _) in keep[1:])
+        want = sum(d["stats"].cpu().numpy().astype(np.int64).sum(axis=1) for (_, d, _, _) in keep)
         np.testing.assert_array_equal(totals.cpu().numpy(), want)
     g.close()
+
+
+@pytest.mark.parametrize("lu", [32, 64])
+def test_mixed_handoff_parity(mc, lu):
+    """A low hand-off threshold sends most thread-per-cell cells of the mixed
+    launch through its record lists and the warp-per-cell pass."""
+    import torch
+    from mc_inputs import mixed_batch
+    batch = mixed_batch(3 * 400, seed=8, hot_fraction=0.01)
+    segs, keep = _segments(mc, batch, MIXED_DTS)
+    mc.mc_burn_mixed(segs, mc.mc_burn_opts_default(lu_precision=lu, straggler_steps=40), 1e10)
+    torch.cuda.synchronize()
+    for (h, d, net, cells), (gx, gT, gs, gst), dt in zip(keep, _snapshot(keep), MIXED_DTS):
+        ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, dt)
+        rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
+        print(net.name, lu, rep)
+        assert rep["pass"], (net.name, rep)
 
 
 def test_results_do_not_depend_on_the_mix(mc):
