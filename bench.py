@@ -47,7 +47,8 @@ PARITY_SAMPLE = 512
 # ---- FP64-pipe roofline model ---------------------------------------------
 # FP64 flops per unit of work (an FMA is 2 flops, an add or a multiply 1).
 # Measured by ncu's thread-level DFMA/DADD/DMUL counters on the library's own
-# evaluation kernels (profiles/fp64_per_unit_eval_kernels.md):
+# evaluation kernels (python -m paper_2608_06466_b300.profile_case eval, 2^18
+# states each):
 #   RHS_FLOPS_PER_REACTION   one reaction of a right-hand side: two table
 #                            exponentials and their arguments, the mass-action
 #                            products, the scatter and the energy term
@@ -61,7 +62,7 @@ PARITY_SAMPLE = 512
 #              sweeps are not counted, so the FP32 figure is a lower bound)
 #   attempt    (q(q+1)/2 + 2(q+1) + 3) n with q = 3, the weights' n reciprocals
 #              charged 1 flop each
-RHS_FLOPS_PER_REACTION = 51.75   # k_rates slope 38.75 (two exponentials with their arguments) + 13
+RHS_FLOPS_PER_REACTION = 51.75   # k_rates slope 38.8 (two exponentials with their arguments) + 13
 RHS_FLOPS_FIXED = 47.0           # k_rhs on net13: 2117 flops per right-hand side = 47 + 40 x 51.75
 
 
@@ -79,10 +80,12 @@ def fp64_flops(S, R, n, stats, lu_precision):
 
 
 # DRAM traffic of the burn's thread-per-cell worker per step attempt, from an
-# ncu capture of its bulk on 2^20 cells (profiles/k_burn_persistent_net13_2p20_bulk.md:
-# 2.088 TB read + written over 243.8 M attempts); the fused kernel runs the same
-# worker, and the traffic (lane state past L2) grows with attempts, not cells.
-DRAM_BYTES_PER_ATTEMPT = 8565.0
+# ncu capture of its bulk on 2^20 net13 cells with the FP32 matrix
+# (python -m paper_2608_06466_b300.profile_case burn --cells 1048576 --lu 32
+# --variant 2 --max-steps 3000 --straggler -1: 2110 GB read + written over
+# 243.8 M attempts); the fused kernel runs the same worker, and the traffic
+# (lane state evicted past L2) grows with attempts, not cells.
+DRAM_BYTES_PER_ATTEMPT = 8656.0
 
 # where the nvidia-smi clock samples of the timed region are written
 LOG_DIR = os.environ.get("MC_BENCH_LOG_DIR", os.path.join(tempfile.gettempdir(), "mc_bench"))
@@ -291,7 +294,10 @@ def run_mixed(args, mc, world, rank, local, stream, flush, barrier, fp64_peak, f
         m = cells["x"].shape[1]
         segs.append(mc.segment(h, m, m, d["x"], d["T"], d["ndens"], d["rate_scale"], d["status"], d["stats"], dt=dt))
         keep.append((h, d, x0, T0, net, cells))
-    opts = mc.mc_burn_opts_default(lu_precision=32)
+    # the FP64 iteration matrix: on this GPU the faster form for these networks
+    # (cooperative FP64 LU; the 33-ODE matrices defeat FP32 refinement late in
+    # a burn and send those cells to the FP64 retry)
+    opts = mc.mc_burn_opts_default(lu_precision=64)
     g = mc.mc_graph_create(segs, opts, DT)
 
     def reset():
@@ -304,13 +310,14 @@ def run_mixed(args, mc, world, rank, local, stream, flush, barrier, fp64_peak, f
         reset()
         g.launch(stream)
 
-    ms, per, launches, clocks = timed_steps(step, args.steps, args.warmup, stream, flush, barrier, rank, local, True)
+    ms, per, launches, clocks, k_timed, w_run = timed_steps(step, args.steps, args.warmup, stream, flush, barrier,
+                                                           rank, local, True, args.max_timed_s, world)
     ms = max_over_ranks(ms, world, "cuda")
     flops, attempts, ok = 0.0, 0.0, 0
     results = []
     for (h, d, x0, T0, net, cells) in keep:
         st = d["stats"].cpu().numpy()
-        flops += fp64_flops(net.n_species, net.n_reactions, net.n_ode, st, 32)
+        flops += fp64_flops(net.n_species, net.n_reactions, net.n_ode, st, 64)
         attempts += float((st[0].astype(np.int64) + st[1] + st[2]).sum())
         s = d["status"].cpu().numpy()
         ok += int((s == 0).sum())
@@ -378,12 +385,13 @@ def run_mixed(args, mc, world, rank, local, stream, flush, barrier, fp64_peak, f
     achieved = flops / (ms / 1e3) / 1e12
     return {
         "metric": METRIC, "value": job_throughput(n, world, ms), "unit": "cells/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "steps": k_timed, "warmup": w_run, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps_requested": args.steps, "warmup_requested": args.warmup,
         "config": {"workload": "batched uneven work: Robertson (3 ODEs, t = 40) + net13 (13 ODEs) + net33 "
                                "(33 ODEs, 4 elements, 120 reactions), a third each, 1 % hot cells T log-U[1e4, 1e5] K",
                    "n_cells_per_gpu": n, "seed": MIXED_SEED + 1000 * rank, "dt_s": list(MIXED_DTS),
-                   "rtol": 1e-6, "atol": 1e-10, "lu_precision": 32,
+                   "rtol": 1e-6, "atol": 1e-10, "lu_precision": 64,
                    "variant": "one persistent launch over all networks (cost-ordered queues, hand-off and "
                               "warp-per-cell record pass), CUDA graph replay",
                    "l2": "inputs exceed L2 and L2 is flushed between steps",
@@ -411,13 +419,26 @@ def _build_if_missing():
         mod.build()
 
 
-def timed_steps(step, steps, warmup, stream, flush, barrier, rank, local, sample_clocks):
+def timed_steps(step, steps, warmup, stream, flush, barrier, rank, local, sample_clocks, budget_s=None, world=1):
     """W untimed and K timed steps, CUDA events on the launching stream, a
-    barrier and a device synchronize on both sides, L2 flushed before each."""
+    barrier and a device synchronize on both sides, L2 flushed before each.
+    With budget_s, at most 3 warm-up steps run and K is cut to what the last
+    warm-up step's time fits in budget_s (at least 3; the same on every rank);
+    the count actually timed is returned."""
     import torch
     import paper_2608_06466_b300 as mc
+    if budget_s is not None:
+        warmup = min(warmup, 3)
+    t_last = 0.0
     for _ in range(warmup):
+        t0 = time.perf_counter()
         step()
+        torch.cuda.synchronize()
+        t_last = time.perf_counter() - t0
+    if budget_s is not None and t_last > 0.0:
+        fit = int(max_over_ranks(budget_s / t_last, world, "cuda") if world == 1 else
+                  -max_over_ranks(-budget_s / t_last, world, "cuda"))
+        steps = max(3, min(steps, fit))
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -438,7 +459,7 @@ def timed_steps(step, steps, warmup, stream, flush, barrier, rank, local, sample
     barrier()
     launches = mc.mc_launch_count()
     clocks = clock_sampler_stop(proc, fh, path, local) if sample_clocks else None
-    return float(np.mean(per)), per, launches, clocks
+    return float(np.mean(per)), per, launches, clocks, steps, warmup
 
 
 def main():
@@ -449,12 +470,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="precision", choices=["precision", "mixed"])
     ap.add_argument("--cells", type=int, default=N_CELLS)
+    ap.add_argument("--max-timed-s", type=float, default=300.0,
+                    help="cut the timed steps to what fits this many seconds (at least 3) and the warm-up to 3; "
+                         "0 times exactly --steps after exactly --warmup")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 comparison arms")
     ap.add_argument("--serving", action="store_true",
                     help="add the serving-loop measurement (AMR-box requests, a few minutes)")
     ap.add_argument("--no-serving", action="store_true", help="no serving measurement (the default)")
     args = ap.parse_args()
+    if args.max_timed_s <= 0:
+        args.max_timed_s = None
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -505,8 +531,9 @@ def main():
         d["T"].copy_(T0)
         mc.mc_burn_batch(h, opts, n, DT, d["x"], n, d["T"], d["ndens"], None, d["status"], d["stats"], stream)
 
-    ms32, per32, launches, clocks = timed_steps(lambda: burn(opts32), args.steps, args.warmup, stream, flush,
-                                                barrier, rank, local, sample_clocks=True)
+    ms32, per32, launches, clocks, k_timed, w_run = timed_steps(lambda: burn(opts32), args.steps, args.warmup, stream,
+                                                                flush, barrier, rank, local, True, args.max_timed_s,
+                                                                world)
     ms32 = max_over_ranks(ms32, world, "cuda")
     gx, gT = d["x"].cpu().numpy(), d["T"].cpu().numpy()
     status = d["status"].cpu().numpy()
@@ -523,7 +550,7 @@ def main():
         small = min(n, 4096)
         for o in (opts64p, opts64):
             mc.mc_burn_batch(h, o, small, DT, d["x"], n, d["T"], d["ndens"], None, d["status"], d["stats"], stream)
-        ms64p, _, _, _ = timed_steps(lambda: burn(opts64p), 1, 0, stream, flush, barrier, rank, local, False)
+        ms64p = timed_steps(lambda: burn(opts64p), 1, 0, stream, flush, barrier, rank, local, False)[0]
         st64p = d["stats"].cpu().numpy()
         cells_p = synthetic_cells(net, N_PLAIN, seed=PLAIN_SEED)
         dp = to_device(cells_p)
@@ -535,7 +562,7 @@ def main():
             mc.mc_burn_batch(h, opts64, N_PLAIN, DT, dp["x"], N_PLAIN, dp["T"], dp["ndens"], None, dp["status"],
                              dp["stats"], stream)
 
-        ms64, _, _, _ = timed_steps(burn_plain, 1, 0, stream, flush, barrier, rank, local, False)
+        ms64 = timed_steps(burn_plain, 1, 0, stream, flush, barrier, rank, local, False)[0]
         st64 = dp["stats"].cpu().numpy()
         arms = {
             "fp64_persistent": {
@@ -558,16 +585,18 @@ def main():
     nh = torch.from_numpy(np.ascontiguousarray(cells["ndens"])).pin_memory()
     xw, Tw = xh.clone().pin_memory(), Th.clone().pin_memory()
     sh = torch.zeros(n, dtype=torch.int32).pin_memory()
+    # one timed call: the kernels, scratch and allocator pool are warm from the
+    # device-resident steps above
     e2e_ms = []
-    for i in range(1 + max(1, min(args.steps, 2))):
+    for _ in range(1):
         xw.copy_(xh)
         Tw.copy_(Th)
         torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         mc.mc_burn_batch(h, opts32, n, DT, xw.numpy(), n, Tw.numpy(), nh.numpy(), None, sh.numpy(), None, None)
         t1 = time.perf_counter()
-        if i > 0:
-            e2e_ms.append((t1 - t0) * 1e3)
+        e2e_ms.append((t1 - t0) * 1e3)
     e2e_v = job_throughput(n, world, max_over_ranks(float(np.mean(e2e_ms)), world, "cuda"))
     h2d = (net.n_species + 2) * 8 * n
     d2h = (net.n_species + 1) * 8 * n + 4 * n
@@ -587,9 +616,10 @@ def main():
         achieved = flops / (ms32 / 1e3) / 1e12
         traffic = None if DRAM_BYTES_PER_ATTEMPT is None else DRAM_BYTES_PER_ATTEMPT * attempts
         line = {
-            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": k_timed,
+            "warmup": w_run, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps_requested": args.steps, "warmup_requested": args.warmup,
             "config": {"workload": "precision form: net13 synthetic kinetics, 12 species from 3 elements + energy "
                                    "equation (13 ODEs), 40 reversible reactions, ideal gas gamma=5/3",
                        "n_cells_per_gpu": n, "cell_seed": shard_seed(rank), "dt_s": DT, "rtol": 1e-6, "atol": 1e-10,

@@ -131,14 +131,22 @@ typedef struct {
 
 void mc_burn_opts_default(mc_burn_opts *opts);
 
-/* Upload a network. The description is copied; the handle stays valid until
- * mc_network_destroy. Errors: MC_E_INVALID (bad indices or sizes),
- * MC_E_UNSUPPORTED (too many ODEs or reactions), MC_E_NOMEM, MC_E_CUDA. */
+/* Upload a network: the network is its own object, separate from the
+ * integrator that uses it (paper: Software design section, paragraph 4). The
+ * description is copied into device constants on the current device; the
+ * handle stays valid until mc_network_destroy. Errors: MC_E_INVALID (bad
+ * indices or sizes), MC_E_UNSUPPORTED (too many ODEs or reactions),
+ * MC_E_NOMEM, MC_E_CUDA. */
 mc_status mc_network_create(const mc_network_desc *desc, mc_network **out);
+/* Free a network's device constants (paragraph 4). NULL is accepted. The
+ * network must not be in use by work still queued on any stream. */
 mc_status mc_network_destroy(mc_network *net);
+/* ODE count of a network: species plus one for the energy equation (paragraph 4). */
 int32_t mc_network_n_ode(const mc_network *net);
 
-/* Burn n_cells cells over dt (seconds) in place.
+/* Burn n_cells cells over dt (seconds) in place: the operator-split reaction
+ * step of each zone, one zone per cell, integrated on the GPU and its failure
+ * handed back per cell (paper: Software design section, paragraphs 3-4).
  *   x          [n_species][ld] in/out number fractions
  *   T          [ld] in/out temperature (K); required when energy_eq, else the
  *              isothermal temperature of each cell or NULL (T = 1)
@@ -200,14 +208,18 @@ mc_status mc_burn_batch_sdc(const mc_network *net, const mc_burn_opts *opts, int
                             double *x, int64_t ld, double *T, const double *ndens, const double *rate_scale,
                             const double *source, int32_t *status, int32_t *stats, void *stream);
 
-/* Rate coefficients of every reaction at n temperatures T[c] (device
+/* Rate coefficients k = A T^b exp(-C/T) of the network (paragraph 4's
+ * network half; BASELINE workloads' rate form) of every reaction at n
+ * temperatures T[c] (device
  * arrays): kf[r * ld + c], kr[r * ld + c] (kr = 0 for irreversible reactions),
  * computed by the burn's own device code (including its table-driven
  * exponential). Asynchronous. Errors: MC_E_INVALID, MC_E_CUDA. */
 mc_status mc_network_rates(const mc_network *net, int64_t n, const double *T, double *kf, double *kr,
                            int64_t ld, void *stream);
 
-/* Right-hand side f(y) (and, if jac != NULL, the analytic Jacobian) of the
+/* Right-hand side f(y) (and, if jac != NULL, the analytic Jacobian, as the
+ * burn's persistent workers evaluate it, one warp per state) -- the network
+ * interface the integrator calls (paragraph 4) -- of the
  * burn's ODE system at n states (device arrays): y[i * ld + c] with the
  * energy form's last component u = (sum x) k_B T / (gamma - 1); T is the
  * isothermal temperature (ignored by energy networks, NULL = 1), ndens and
@@ -261,24 +273,29 @@ typedef struct {
     double dt;
 } mc_segment;
 
-/* Burn several segments (different networks, uneven stiffness) in ONE
+/* Burn several segments (different networks, uneven stiffness, each with its
+ * own dt) in ONE
  * persistent launch: workers pull cells from per-network queues, and a lane
  * whose cell finishes takes the next cell (paper: divergence between zones,
  * Software design section, paragraph 3). Asynchronous on stream. */
 mc_status mc_burn_mixed(const mc_segment *segs, int32_t n_segs, const mc_burn_opts *opts,
                         double dt, void *stream);
 
-/* Capture mc_burn_mixed for fixed segments into a CUDA graph (queue reset,
+/* Capture mc_burn_mixed for fixed segments into a CUDA graph (paragraph 3's
+ * zone loop as one replayable unit of GPU work: queue reset,
  * persistent launch, counter reduction) and replay it with mc_graph_launch.
  * The segment arrays must stay allocated while the graph exists; their
  * contents may change between launches. totals (may be NULL) receives, after
  * each replay, the MC_NSTAT counters summed over all cells (device int64[8]). */
 mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, const mc_burn_opts *opts,
                           double dt, int64_t *totals, void *stream, mc_graph **out);
+/* Replay a captured mixed burn on stream (asynchronous). Errors: MC_E_INVALID, MC_E_CUDA. */
 mc_status mc_graph_launch(mc_graph *g, void *stream);
+/* Free a graph and the scratch its replays use (waits for the device). */
 mc_status mc_graph_destroy(mc_graph *g);
 
-/* Measure every launch shape (plain or persistent x threads per block x
+/* Autotune the zone loop of paragraph 3 on this GPU: measure every launch
+ * shape (plain or persistent x threads per block x
  * persistent blocks per SM) on a sample of n_sample cells (device arrays laid
  * out as in mc_burn_batch; they are copied, not modified) and keep the fastest
  * for this network size and opts->lu_precision: later burns whose shape
@@ -341,7 +358,10 @@ mc_status mc_server_drain(mc_server *srv, double timeout_s);
 mc_status mc_server_destroy(mc_server *srv);
 
 /* ---------------------------------------------------------------- misc */
+/* Library services with no counterpart in the paper. */
+/* Message of this thread's last error (empty when none); owned by the library. */
 const char *mc_last_error(void);
+/* ABI version of this header and library. */
 int32_t mc_version(void);
 /* Kernel launches issued by this thread since the last reset (for accounting). */
 int64_t mc_launch_count(int32_t reset);
@@ -354,6 +374,34 @@ int64_t mc_alloc_count(void);
  * (about 10 ms each): the ceiling this ALU-bound burn is reported against.
  * Either pointer may be NULL. Synchronous. Errors: MC_E_CUDA, MC_E_NOMEM. */
 mc_status mc_probe_fma_rate(double *tflops_fp64, double *tflops_fp32);
+
+/* Bounds-check build. libmc_check.so is this library compiled with
+ * -DMC_BOUNDS_CHECK: every cell index, list position and straggler-record
+ * index a burn kernel computes is tested before the access it guards; a
+ * refused access is counted (the first one recorded) and skipped instead of
+ * faulting, and mc_burn_batch, mc_burn_batch_sdc and mc_burn_ladder count each
+ * cell's final store and verify on the device, after the call, that every
+ * cell was stored exactly once (the queue handed every cell out once; the
+ * hand-off, retry lists and rungs lost and duplicated none). Store counting
+ * assumes one such call at a time per device. In the normal build nothing is
+ * checked and the report has enabled = 0. */
+typedef struct mc_bounds_info {
+  int32_t enabled;          /* 1 in the bounds-check build */
+  uint32_t refused;         /* accesses refused since the last reset */
+  int32_t first_site;       /* site of the first refused access (0: none): 1 cell load, 2 cell
+                               store, 3 list read, 4 list push, 5 record, 6 warp-form load, 7 RKC */
+  int32_t pad;
+  int64_t first_index;      /* its index */
+  int64_t first_bound;      /* and bound */
+  int64_t calls_checked;    /* calls whose stores were verified */
+  int64_t cells_checked;    /* cells over those calls */
+  int64_t cells_not_once;   /* cells of those calls not stored exactly once */
+} mc_bounds_info;
+/* The device's record (synchronises the device). Errors: MC_E_INVALID (null
+ * out), MC_E_CUDA. */
+mc_status mc_bounds_report(int32_t device, mc_bounds_info *out);
+/* Zero the device's record (synchronises the device). */
+mc_status mc_bounds_reset(int32_t device);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,8 @@ Argument marshalling only: every step of the burn runs in the library's CUDA
 kernels. Cell arrays may be torch CUDA tensors (device path, asynchronous on
 the given stream) or numpy arrays / CPU tensors (host path, synchronous). If
 libmc.so is missing or cannot be loaded, importing this module raises.
+MC_LIBRARY, when set, names the library file to load instead (the
+bounds-check build libmc_check.so, for instance).
 """
 from __future__ import annotations
 
@@ -13,7 +15,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmc.so")
+LIB_PATH = os.environ.get("MC_LIBRARY") or os.path.join(_HERE, "libmc.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2608_06466_b300/build.py` "
@@ -60,6 +62,12 @@ class mc_request_info(C.Structure):
     _fields_ = [("state", C.c_int32), ("n_failed", C.c_int32), ("n_cells", C.c_int64),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
                 ("gpu_start", C.c_double), ("gpu_end", C.c_double)]
+
+
+class mc_bounds_info(C.Structure):
+    _fields_ = [("enabled", C.c_int32), ("refused", C.c_uint32), ("first_site", C.c_int32), ("pad", C.c_int32),
+                ("first_index", C.c_int64), ("first_bound", C.c_int64), ("calls_checked", C.c_int64),
+                ("cells_checked", C.c_int64), ("cells_not_once", C.c_int64)]
 
 
 def _sig(name, res, args):
@@ -113,6 +121,8 @@ _sig("mc_network_rhs", C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
 _sig("mc_autotune", C.c_int32, [C.c_void_p, C.POINTER(mc_burn_opts), C.c_int64, C.c_double, C.c_void_p, C.c_int64,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(mc_burn_opts)])
 _sig("mc_probe_fma_rate", C.c_int32, [C.POINTER(C.c_double), C.POINTER(C.c_double)])
+_sig("mc_bounds_report", C.c_int32, [C.c_int32, C.POINTER(mc_bounds_info)])
+_sig("mc_bounds_reset", C.c_int32, [C.c_int32])
 
 
 class MCError(RuntimeError):
@@ -364,6 +374,17 @@ def mc_probe_fma_rate():
 
 def mc_launch_count(reset: bool = False) -> int:
     return int(lib.mc_launch_count(1 if reset else 0))
+
+
+def mc_bounds_report(device: int = 0) -> dict:
+    """The bounds-check record of a device (enabled = 0 in the normal build)."""
+    info = mc_bounds_info()
+    check(lib.mc_bounds_report(device, C.byref(info)), "mc_bounds_report")
+    return {f: getattr(info, f) for f, _ in mc_bounds_info._fields_ if f != "pad"}
+
+
+def mc_bounds_reset(device: int = 0) -> None:
+    check(lib.mc_bounds_reset(device), "mc_bounds_reset")
 
 
 def mc_alloc_count() -> int:

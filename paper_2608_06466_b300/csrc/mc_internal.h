@@ -49,6 +49,12 @@ void scratch_free(void *h);
 mc_status scratch_get(int dev, int64_t retry_cells, unsigned long long **next, uint32_t **rcount,
                       int32_t **retry);
 mc_status burn_device(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st);
+// Bounds-check build (mc_check.cu; no-ops in the normal build): give a
+// launch's cell arguments the device's check record, and bracket a call whose
+// every cell must be stored exactly once.
+void bc_attach(CellArgs &a);
+mc_status bc_begin(int64_t n_cells, cudaStream_t st);
+mc_status bc_end(int64_t n_cells, cudaStream_t st);
 // Burn with the explicit Runge-Kutta-Chebyshev integrator (mc_rkc.cu).
 mc_status burn_rkc_device(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st);
 mc_status burn_device_scratch(const mc_network *net, const mc_burn_opts &o, const CellArgs &a, cudaStream_t st,

@@ -4,6 +4,7 @@
 // divergence the paper's Software design section, paragraph 3, names).
 #pragma once
 
+#include "mc_check.cuh"
 #include "mc_coop.cuh"
 
 namespace mc {
@@ -30,6 +31,10 @@ struct CellArgs {
   uint32_t lretry_mask;     // statuses that go to lretry
   int32_t *rung;            // retry ladder: rung that wrote each cell's outputs, or nullptr
   int32_t rung_id;
+#ifdef MC_BOUNDS_CHECK
+  BoundsCheck *bc;          // the device's check record
+  int64_t cells;            // cells of the call (bound of cell indices and list positions; 0: n_cells)
+#endif
 };
 
 // statuses an FP32-matrix pass hands to its FP64 retry pass
@@ -48,13 +53,14 @@ __device__ __forceinline__ int route_of(const CellArgs &a, int &status) {
   return 0;
 }
 
-__device__ __forceinline__ void push_list(int32_t *list, uint32_t *count, int64_t c) {
+__device__ __forceinline__ void push_list(const CellArgs &a, int32_t *list, uint32_t *count, int64_t c) {
   const uint32_t k = atomicAdd(count, 1u);
-  list[k] = (int32_t)c;
+  if (MC_IN(a, BC_LIST_PUSH, k, MC_CELLS(a))) list[k] = (int32_t)c;
 }
 
 __device__ __forceinline__ int64_t cell_of(const CellArgs &a, int64_t k) {
-  return a.index ? (int64_t)a.index[k] : k;
+  if (!a.index) return k;
+  return MC_IN(a, BC_LIST_READ, k, MC_CELLS(a)) ? (int64_t)a.index[k] : -1;
 }
 
 __device__ __forceinline__ int64_t count_of(const CellArgs &a) {
@@ -69,6 +75,12 @@ template <int N, typename LT>
 __device__ void load_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a, int64_t c) {
   const int S = net.S, n = net.n;
   L.cell = c;
+  if (!MC_IN(a, BC_CELL_LOAD, c, MC_CELLS(a))) {
+    L.status = CELL_BAD_INPUT;
+    L.phase = PH_DONE;
+    L.m = -1;
+    return;
+  }
   L.status = CELL_OK;
   L.q = 0;
   L.kept = false;
@@ -126,8 +138,10 @@ __device__ void store_cell(Lane<N, LT> &L, const DNet &net, const CellArgs &a) {
   const int64_t c = L.cell;
   const int S = net.S;
   const int route = route_of(a, L.status);
-  if (route == 1) { push_list(a.retry, a.retry_count, c); return; }
-  if (route == 2) { push_list(a.lretry, a.lretry_count, c); return; }
+  if (route == 1) { push_list(a, a.retry, a.retry_count, c); return; }
+  if (route == 2) { push_list(a, a.lretry, a.lretry_count, c); return; }
+  if (!MC_IN(a, BC_CELL_STORE, c, MC_CELLS(a))) return;
+  MC_STORED(a, c);
   if (a.rung) a.rung[c] = a.rung_id;
   const bool rejected = (L.status == CELL_BAD_INPUT && L.m < 0);
   if (!rejected) {

@@ -194,8 +194,8 @@ DNet mc::dnet_of(const mc_network *net) {
 // ---------------------------------------------------------------- device scratch
 // Library-owned scratch, one set per (device, stream) so burns issued on
 // different streams never share queue counters or lists: the persistent queue
-// counters, the FP32 pass's retry lists and the straggler records (each grown
-// on demand, never shrunk).
+// counters, the FP32 pass's retry lists, the cost order, the straggler records
+// and the retry ladder's lists (each grown on demand, never shrunk).
 namespace {
 struct DevScratch {
   unsigned long long *next = nullptr;   // [MAX_QUEUES] queue counters
@@ -219,13 +219,16 @@ DevScratch &scratch_of(int dev) {
   return g_scratch[std::make_pair(dev, (uintptr_t)g_cur_stream)];
 }
 
-// the old buffer may still be read by work queued on this stream
+// Scratch grows by stream-ordered allocation on its own stream: the old
+// buffer is freed after the work already queued on the stream (which may
+// still read it), and neither step synchronises the device, so a burn on one
+// stream never waits for burns on others.
 cudaError_t retire(void *p) {
   if (!p) return cudaSuccess;
-  cudaError_t e = cudaStreamSynchronize(g_cur_stream);
-  cudaFree(p);
-  return e;
+  return cudaFreeAsync(p, g_cur_stream);
 }
+
+cudaError_t grow(void **p, size_t bytes) { return dev_malloc_async(p, bytes, g_cur_stream); }
 }  // namespace
 
 void mc::scratch_stream(cudaStream_t st) { g_cur_stream = st; }
@@ -260,7 +263,7 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
   DevScratch &s = scratch_of(dev);
   cudaError_t e;
   if (!s.next) {
-    e = dev_malloc((void **)&s.next, (sizeof(unsigned long long) + sizeof(uint32_t)) * MAX_QUEUES);
+    e = grow((void **)&s.next, (sizeof(unsigned long long) + sizeof(uint32_t)) * MAX_QUEUES);
     if (e != cudaSuccess) return cuda_error(e, "scratch allocation");
     s.retry_count = (uint32_t *)(s.next + MAX_QUEUES);
   }
@@ -269,7 +272,7 @@ mc_status mc::scratch_get(int dev, int64_t retry_cells, unsigned long long **nex
     s.retry = nullptr;
     s.retry_cap = 0;
     if (e != cudaSuccess) return cuda_error(e, "scratch grow sync");
-    e = dev_malloc((void **)&s.retry, sizeof(int32_t) * retry_cells);
+    e = grow((void **)&s.retry, sizeof(int32_t) * retry_cells);
     if (e != cudaSuccess) return cuda_error(e, "retry list allocation");
     s.retry_cap = retry_cells;
   }
@@ -286,7 +289,7 @@ mc_status mc::straggler_scratch(size_t bytes, void **rec, uint32_t **count) {
   DevScratch &s = scratch_of(dev);
   cudaError_t e;
   if (!s.rec_count) {
-    e = dev_malloc((void **)&s.rec_count, 256);
+    e = grow((void **)&s.rec_count, 256);
     if (e != cudaSuccess) return cuda_error(e, "straggler counter allocation");
   }
   if (bytes > s.rec_bytes) {
@@ -294,7 +297,7 @@ mc_status mc::straggler_scratch(size_t bytes, void **rec, uint32_t **count) {
     s.rec = nullptr;
     s.rec_bytes = 0;
     if (e != cudaSuccess) return cuda_error(e, "straggler grow sync");
-    e = dev_malloc((void **)&s.rec, bytes);
+    e = grow((void **)&s.rec, bytes);
     if (e != cudaSuccess) return cuda_error(e, "straggler record allocation");
     s.rec_bytes = bytes;
   }
@@ -311,7 +314,7 @@ mc_status mc::ladder_scratch(int dev, int64_t n, int32_t **lists, uint32_t **cou
     s.ladder = nullptr;
     s.ladder_cap = 0;
     if (e != cudaSuccess) return cuda_error(e, "ladder grow sync");
-    e = dev_malloc(&s.ladder, 256 + sizeof(int32_t) * 2 * (size_t)n);
+    e = grow(&s.ladder, 256 + sizeof(int32_t) * 2 * (size_t)n);
     if (e != cudaSuccess) return cuda_error(e, "ladder list allocation");
     s.ladder_cap = n;
   }
@@ -330,7 +333,7 @@ mc_status mc::order_scratch(int dev, int64_t n, int32_t **index, uint8_t **bkt, 
     s.order = nullptr;
     s.order_cap = 0;
     if (e != cudaSuccess) return cuda_error(e, "order grow sync");
-    e = dev_malloc((void **)&s.order, list + bytes + sizeof(uint32_t) * ORDER_BUCKETS);
+    e = grow((void **)&s.order, list + bytes + sizeof(uint32_t) * ORDER_BUCKETS);
     if (e != cudaSuccess) return cuda_error(e, "order buffer allocation");
     s.order_cap = n;
   }
@@ -434,6 +437,7 @@ mc_status mc::burn_device(const mc_network *net, const mc_burn_opts &ob, const C
   if (s != MC_OK) return s;
   // queue-fed launches hand out the cells in decreasing cost order
   CellArgs a = a0;
+  bc_attach(a);
   if (!a0.index && !a0.n_dev && autotune_pick(net, ob).variant != MC_VARIANT_PLAIN) {
     int32_t *order;
     uint8_t *bkt;
@@ -499,7 +503,10 @@ mc_status burn_batch_impl(const mc_network *net, const mc_burn_opts *opts, int64
     a.src = source;
     a.status = status;
     a.stats = stats;
-    return burn_device(net, o, a, st);
+    s = bc_begin(n_cells, st);
+    if (s == MC_OK) s = burn_device(net, o, a, st);
+    if (s == MC_OK) s = bc_end(n_cells, st);
+    return s;
   }
   // host arrays: stage through device memory, packed with ld = n_cells
   const int64_t nc = n_cells;
@@ -531,7 +538,9 @@ mc_status burn_batch_impl(const mc_network *net, const mc_burn_opts *opts, int64
   if (e == cudaSuccess && rate_scale) e = h2d((void *)a.ks, rate_scale, net->R);
   if (e == cudaSuccess && source) e = h2d((void *)a.src, source, net->n);
   if (e != cudaSuccess) { cudaFreeAsync(buf, st); return cuda_error(e, "host to device copy"); }
-  s = burn_device(net, o, a, st);
+  s = bc_begin(n_cells, st);
+  if (s == MC_OK) s = burn_device(net, o, a, st);
+  if (s == MC_OK) s = bc_end(n_cells, st);
   if (s != MC_OK) { cudaFreeAsync(buf, st); return s; }
   e = cudaMemcpy2DAsync(x, sizeof(double) * ld, a.x, sizeof(double) * nc, sizeof(double) * nc, net->S,
                         cudaMemcpyDeviceToHost, st);
@@ -632,6 +641,9 @@ extern "C" mc_status mc_burn_ladder(const mc_network *net, const mc_rung *rungs,
   base.status = status;
   base.stats = stats;
   base.rung = rung;
+  bc_attach(base);
+  s = bc_begin(n_cells, st);
+  if (s != MC_OK) return s;
   for (int k = 0; k < n_rungs; ++k) {
     CellArgs a = base;
     a.rung_id = k;
@@ -651,5 +663,5 @@ extern "C" mc_status mc_burn_ladder(const mc_network *net, const mc_rung *rungs,
     s = (rungs[k].method == MC_METHOD_RKC) ? burn_rkc_device(net, ro[k], a, st) : burn_device(net, ro[k], a, st);
     if (s != MC_OK) return s;
   }
-  return MC_OK;
+  return bc_end(n_cells, st);
 }

@@ -205,6 +205,7 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     a.ks = g.rate_scale;
     a.status = g.status;
     a.stats = g.stats;
+    bc_attach(a);
     // each segment's queue hands out its cells in decreasing cost order
     if (g.n_cells > 0) {
       rs = order_cells(g.net, o, a, order + off, bkt + off, hist, st);
@@ -326,6 +327,11 @@ extern "C" mc_status mc_graph_create(const mc_segment *segs, int32_t n_segs, con
   scratch_stream(cs);
   s = scratch_get(dev, o.lu_precision == 32 ? total : 0, &next, &rcount, &retry);
   if (s == MC_OK) s = mixed_reserve(segs, n_segs, o, cs);
+  if (s == MC_OK) {
+    // the stream-ordered scratch must exist before replays on other streams use it
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) s = cuda_error(e, "capture stream set-up");
+  }
   if (s != MC_OK) {
     cudaStreamDestroy(cs);
     return s;

@@ -73,6 +73,7 @@ extern "C" mc_status mc_burn_batch_noalloc(const mc_network *net, const mc_burn_
   a.ks = rate_scale;
   a.status = status;
   a.stats = stats;
+  bc_attach(a);
   mc_burn_opts q = o;
   q.variant = MC_VARIANT_PERSISTENT;
   // the counters and the retry count are cleared on the stream by the launches

@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(128) k_burn_rkc(DNet net, Opts o, CellArgs a, 
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= count_of(a)) return;
   const int64_t c = cell_of(a, k);
+  if (!MC_IN(a, BC_RKC_CELL, c, MC_CELLS(a))) return;
   const int S = net.S, n = net.n;
   // inputs, checked as load_cell checks them
   double y[N];
@@ -253,8 +254,9 @@ __global__ void __launch_bounds__(128) k_burn_rkc(DNet net, Opts o, CellArgs a, 
       if (!isfinite(y[i])) status = CELL_NONFINITE;
   }
   const int route = route_of(a, status);
-  if (route == 1) { push_list(a.retry, a.retry_count, c); return; }
-  if (route == 2) { push_list(a.lretry, a.lretry_count, c); return; }
+  if (route == 1) { push_list(a, a.retry, a.retry_count, c); return; }
+  if (route == 2) { push_list(a, a.lretry, a.lretry_count, c); return; }
+  MC_STORED(a, c);
   if (good) {
     double Xo = 0.0;
     for (int i = 0; i < S; ++i) {
@@ -312,8 +314,10 @@ void launch_rkc(const DNet &d, const Opts &o, const CellArgs &a, const double *b
 
 }  // namespace
 
-mc_status mc::burn_rkc_device(const mc_network *net, const mc_burn_opts &ob, const CellArgs &a, cudaStream_t st) {
-  if (a.n_cells <= 0) return MC_OK;
+mc_status mc::burn_rkc_device(const mc_network *net, const mc_burn_opts &ob, const CellArgs &a0, cudaStream_t st) {
+  if (a0.n_cells <= 0) return MC_OK;
+  CellArgs a = a0;
+  bc_attach(a);
   int dev = 0;
   cudaGetDevice(&dev);
   double *beta;

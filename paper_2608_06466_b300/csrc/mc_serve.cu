@@ -12,8 +12,8 @@
 // are on the GPU are admitted as soon as memory and a stream allow and start
 // at once on their own stream, so the work of several requests overlaps on
 // the device. Failed cells are counted on the device; completion is detected
-// with events, and each request records when its work started and ended on
-// the GPU. No device code waits on the host (paper: state resident in GPU
+// with events (the results are copied back once a request's burn has ended),
+// and each request records when its burn started and ended on the GPU. No device code waits on the host (paper: state resident in GPU
 // memory, Software design section, paragraph 3).
 #include <algorithm>
 #include <chrono>
@@ -52,7 +52,8 @@ struct Request {
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0, gpu_start = 0.0, gpu_end = 0.0;
   int stream = -1;
   char *dev = nullptr;          // pooled device state
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timed: start and end of its work on the stream
+  CellArgs args{};              // the burn's view of the pooled state
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timed: start and end of its burn on the stream
   std::string err;
 };
 
@@ -100,10 +101,14 @@ struct mc_server {
 
 namespace {
 
-// Admit one request: device state from the pool, copies in, burn, failed-cell
-// count, copies out, events -- all on the request's stream. Runs on the server
-// thread without the server lock. On failure everything it allocated is
-// released and the message is kept with the request.
+// Admit one request: device state from the pool, copies in, burn and the
+// failed-cell count, then an event marking the end of its GPU work -- all on
+// the request's stream. Runs on the server thread without the server lock and
+// returns as soon as the work is queued; the results are copied out by
+// finish_copies once that event has fired (a copy to pageable host memory
+// would otherwise hold the server thread until the burn ends). On failure
+// everything it allocated is released and the message is kept with the
+// request.
 mc_status start_request(mc_server *s, Request &r) {
   const cudaStream_t st = s->streams[r.stream];
   const int64_t n = r.n;
@@ -118,7 +123,8 @@ mc_status start_request(mc_server *s, Request &r) {
   }
   size_t off = 0;
   auto take = [&](size_t b) { char *p = r.dev + off; off += (b + 255) & ~(size_t)255; return p; };
-  CellArgs a{};
+  CellArgs &a = r.args;
+  a = CellArgs{};
   a.n_cells = n;
   a.ld = n;
   a.dt = r.dt;
@@ -143,20 +149,32 @@ mc_status start_request(mc_server *s, Request &r) {
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(s->fail_host + r.stream, s->fail_dev + r.stream, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(r.x, sizeof(double) * r.ld, a.x, sizeof(double) * n, sizeof(double) * n, S,
-                            cudaMemcpyDefault, st);
-    if (e == cudaSuccess && r.T) e = cudaMemcpyAsync(r.T, a.T, sizeof(double) * n, cudaMemcpyDefault, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(r.status, a.status, sizeof(int32_t) * n, cudaMemcpyDefault, st);
-    if (e != cudaSuccess) ms = cuda_error(e, "server copy out");
+    if (e == cudaSuccess) e = cudaEventRecord(r.ev1, st);
+    if (e != cudaSuccess) ms = cuda_error(e, "server burn");
   }
-  cudaFreeAsync(r.dev, st);
-  r.dev = nullptr;
-  if (ms == MC_OK) {
-    e = cudaEventRecord(r.ev1, st);
-    if (e != cudaSuccess) ms = cuda_error(e, "server completion event");
+  if (ms != MC_OK) {
+    cudaFreeAsync(r.dev, st);
+    r.dev = nullptr;
   }
   return ms;
+}
+
+// The results of a request whose GPU work has ended: copies out (pageable
+// host destinations make these synchronous, now only for the copy itself),
+// the pool memory back, and the stream drained of the copies.
+mc_status finish_copies(mc_server *s, Request &r) {
+  const cudaStream_t st = s->streams[r.stream];
+  const int64_t n = r.n;
+  const int S = r.net->S;
+  const CellArgs &a = r.args;
+  cudaError_t e = cudaMemcpy2DAsync(r.x, sizeof(double) * r.ld, a.x, sizeof(double) * n, sizeof(double) * n, S,
+                                    cudaMemcpyDefault, st);
+  if (e == cudaSuccess && r.T) e = cudaMemcpyAsync(r.T, a.T, sizeof(double) * n, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r.status, a.status, sizeof(int32_t) * n, cudaMemcpyDefault, st);
+  cudaFreeAsync(r.dev, st);
+  r.dev = nullptr;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? MC_OK : cuda_error(e, "server copy out");
 }
 
 double gpu_seconds(cudaEvent_t ref, cudaEvent_t ev) {
@@ -220,7 +238,12 @@ void server_loop(mc_server *s) {
         r.n_failed = (int32_t)s->fail_host[r.stream];
         r.gpu_start = gpu_seconds(s->ref, r.ev0);
         r.gpu_end = gpu_seconds(s->ref, r.ev1);
-        r.state = MC_OK;
+        lk.unlock();
+        const mc_status ms = finish_copies(s, r);
+        const std::string msg = ms == MC_OK ? std::string() : std::string(mc_last_error());
+        lk.lock();
+        r.state = ms;
+        r.err = msg;
       } else {
         r.state = MC_E_CUDA;
         r.err = cudaGetErrorString(q);

@@ -100,6 +100,12 @@ __device__ __forceinline__ void w_load_cell(WState<N> &W, const DNet &net, const
   W.status = CELL_OK;
   W.q = 0;
   for (int k = 0; k < NSTAT; ++k) W.st[k] = 0;
+  if (!MC_IN(a, BC_WARP_LOAD, c, MC_CELLS(a))) {
+    W.status = CELL_BAD_INPUT;
+    W.phase = PH_DONE;
+    W.m = -1;
+    return;
+  }
   bool bad = false;
   double xs = 0.0;
 #pragma unroll
@@ -704,12 +710,14 @@ __device__ __forceinline__ void w_store(WState<N> &W, const DNet &net, const Cel
   const int route = route_of(a, W.status);
   if (route != 0) {
     if (ln == 0) {
-      if (route == 1) push_list(a.retry, a.retry_count, c);
-      else push_list(a.lretry, a.lretry_count, c);
+      if (route == 1) push_list(a, a.retry, a.retry_count, c);
+      else push_list(a, a.lretry, a.lretry_count, c);
     }
     __syncwarp();
     return;
   }
+  if (!MC_IN(a, BC_CELL_STORE, c, MC_CELLS(a))) return;
+  if (ln == 0) MC_STORED(a, c);
   if (a.rung && ln == 0) a.rung[c] = a.rung_id;
   if (!(W.status == CELL_BAD_INPUT && W.m < 0)) {
     double xs = 0.0;
@@ -825,6 +833,7 @@ __global__ void __launch_bounds__(128) k_burn_straggler(DNet net, Opts o, CellAr
     k = __shfl_sync(WFULL, k, 0);
     if (k >= total) break;
     if (__shfl_sync(WFULL, skip, 0)) continue;
+    if (!MC_IN(a, BC_RECORD, k, cap)) continue;
     WState<N> W;
     w_load<N, LT>(W, rec[k], sh, net);
     while (W.phase != PH_DONE) {
@@ -894,6 +903,7 @@ __device__ __forceinline__ void fused_records(const DNet &net, const Opts &o, co
     j = __shfl_sync(WFULL, j, 0);
     if (j >= sa.cap) return;
     if (fuse_wait(sa, fa, j, next) != 1) return;
+    if (!MC_IN(a, BC_RECORD, j, sa.cap)) return;
     // every lane observes the flag, then fences: it synchronises with the
     // release store of the record's writer before reading the record
     (void)ld_relaxed(&sa.flag[j]);

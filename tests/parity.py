@@ -36,7 +36,9 @@ cells). So each cell is classified by the oracle itself:
              by that bar alone.
 
 Statuses must agree except for cells whose oracle attempt count is within 1 %
-of the step cap.
+of the step cap, and, with a re-probe, cells whose oracle status itself moves
+under rounding-level input perturbations (several statuses are then correct;
+reported as "status_excused").
 
 The FP32-matrix form is held to the same rule: its solves are refined with
 FP64 residuals until they match the FP64 solve, so it takes the FP64 form's
@@ -123,24 +125,32 @@ def compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable=None, tight=None, atol
     args = (g_x, g_T, g_s, o_x, o_T, o_s, o_stats)
     if stable is None:
         stable = np.ones(g_s.size, dtype=bool)
-    rep = _compare(*args, stable, tight, atol, max_steps, rtol)
-    miss = np.flatnonzero(rep.pop("_strict_miss"))
+    rep = _compare(*args, stable, tight, atol, max_steps, rtol, None)
+    miss = np.flatnonzero(rep.pop("_strict_miss") | rep.pop("_status_miss"))
     rep["reclassified"] = 0
+    rep["status_excused"] = 0
     if reprobe is None or miss.size == 0:
         return rep
+    # the extended classification: a cell whose oracle result or status moves
+    # under rounding-level perturbations has several correct results
     moved = reprobe(miss)
     stable = stable.copy()
     stable[miss[moved]] = False
-    rep = _compare(*args, stable, tight, atol, max_steps, rtol)
+    excused = np.zeros(g_s.size, dtype=bool)
+    excused[miss[moved]] = True
+    rep = _compare(*args, stable, tight, atol, max_steps, rtol, excused)
     rep.pop("_strict_miss")
+    rep.pop("_status_miss")
     rep["reclassified"] = int(moved.sum())
     return rep
 
 
-def _compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable, tight, atol, max_steps, rtol):
+def _compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable, tight, atol, max_steps, rtol, excused):
     n = g_s.size
     near_cap = o_stats[0] + o_stats[1] + o_stats[2] >= 0.99 * max_steps
     status_bad = (g_s != o_s) & ~near_cap
+    if excused is not None:
+        status_bad &= ~excused
     both_ok = (g_s == 0) & (o_s == 0)
     dx = np.abs(g_x - o_x)
     strict = both_ok & stable
@@ -178,6 +188,9 @@ def _compare(g_x, g_T, g_s, o_x, o_T, o_s, o_stats, stable, tight, atol, max_ste
         rep["sensitive_pass"] = bool(med_ok and p90_ok and not worst.any())
         x_bad[np.flatnonzero(sens)[worst]] = True
     rep["_strict_miss"] = (x_bad | T_bad) & strict
+    rep["_status_miss"] = status_bad
+    if excused is not None:
+        rep["status_excused"] = int((excused & (g_s != o_s)).sum())
     rep["x_fail"] = int(x_bad.sum())
     rep["T_fail"] = int(T_bad.sum())
     rep["pass"] = (rep["status_mismatch"] == 0 and rep["x_fail"] == 0 and rep["T_fail"] == 0

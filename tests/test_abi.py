@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -17,12 +19,19 @@ def _declared():
     return names
 
 
-def test_library_exports_every_declared_symbol():
-    # built at session start (tests/conftest.py)
-    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2608_06466_b300", "libmc.so"))
+@pytest.mark.parametrize("name", ["libmc.so", "libmc_check.so"])
+def test_library_exports_every_declared_symbol(name):
+    # both builds are made at session start (tests/conftest.py)
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2608_06466_b300", name))
     missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
     assert not missing, f"declared in include/ but not exported: {missing}"
     assert lib.mc_version() >= 1
+
+
+def test_normal_build_checks_nothing_without_gpu():
+    import paper_2608_06466_b300 as mc
+    rep = mc.mc_bounds_report(0)
+    assert rep["enabled"] == 0 and rep["refused"] == 0 and rep["calls_checked"] == 0
 
 
 def test_opts_default_and_last_error_without_gpu():

@@ -1,0 +1,56 @@
+"""The bounds-check build (libmc_check.so: the library compiled with
+-DMC_BOUNDS_CHECK). Every launch form runs on small cases in a child process
+that loads the check build; its record must show no refused access and every
+cell of every verified call stored exactly once, and its results must equal
+the normal build's bit for bit (the checks change no arithmetic)."""
+import importlib.util
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CASE = os.path.join(ROOT, "tests", "bounds_case.py")
+
+
+def _build_check_library():
+    spec = importlib.util.spec_from_file_location("_mc_build", os.path.join(ROOT, "paper_2608_06466_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build(check=True)
+
+
+def test_bounds_check_build_is_clean_and_matches(tmp_path):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib = _build_check_library()
+    out = tmp_path / "check.npz"
+    env = dict(os.environ, MC_LIBRARY=lib)
+    r = subprocess.run([sys.executable, CASE, str(out)], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-4000:]
+    chk = dict(np.load(out))
+    assert str(chk["library"]).endswith("libmc_check.so")
+    rep = {k[len("report."):]: int(v) for k, v in chk.items() if k.startswith("report.")}
+    assert rep["enabled"] == 1
+    assert rep["refused"] == 0, rep
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bounds_case
+    assert rep["calls_checked"] == len(bounds_case.VERIFIED), rep
+    assert rep["cells_checked"] == sum(n for _, n in bounds_case.VERIFIED), rep
+    assert rep["cells_not_once"] == 0, rep
+
+    import paper_2608_06466_b300 as mc
+    assert mc.mc_bounds_report(0)["enabled"] == 0  # the normal build checks nothing
+    ref = bounds_case.run_cases(mc)
+    assert set(ref) == {k for k in chk if "." in k and not k.startswith("report.")}
+    for k, v in ref.items():
+        np.testing.assert_array_equal(chk[k], v, err_msg=k)
+    # every cell got a status; padding past n untouched
+    for name, n in bounds_case.VERIFIED:
+        st = ref[f"{name}.st"]
+        assert (st[:n] >= 0).all() and (st[n:] == -7).all(), name

@@ -40,7 +40,7 @@ def _burn_sdc(mc, net, cells, src, dt, **opt):
 def test_sources_match_the_oracle(mc, lu, variant):
     net = network_13()
     cells = synthetic_cells(net, 2048, seed=21)
-    src = synthetic_sources(net, cells, 1e10, seed=22)
+    src = synthetic_sources(net, cells, 1e10, seed=22, scale=0.05)
     gx, gT, gs, gst = _burn_sdc(mc, net, cells, src, 1e10, lu_precision=lu, variant=variant)
     on = oracle.OracleNetwork(net)
     (ox, oT, os_, ost), stable, rp = classify(on, cells, 1e10, oracle.burn, with_reprobe=True, source=src)
