@@ -79,13 +79,13 @@ def fp64_flops(S, R, n, stats, lu_precision):
     return float((st[3] * f_rhs + st[4] * f_jac + st[5] * f_lu + st[6] * f_solve + attempts * f_step).sum())
 
 
-# DRAM traffic of the burn's thread-per-cell worker per step attempt, from an
-# ncu capture of its bulk on 2^20 net13 cells with the FP32 matrix
+# DRAM traffic of the headline kernel (k_burn_fused<13, float>) per step
+# attempt, from an ncu capture of one launch on 2^20 net13 cells
 # (python -m paper_2608_06466_b300.profile_case burn --cells 1048576 --lu 32
-# --variant 2 --max-steps 3000 --straggler -1: 2110 GB read + written over
-# 243.8 M attempts); the fused kernel runs the same worker, and the traffic
-# (lane state evicted past L2) grows with attempts, not cells.
-DRAM_BYTES_PER_ATTEMPT = 8656.0
+# --variant 2 --max-steps 3000: 2005.7 GB read + written over 243.8 M
+# attempts); the traffic is lane state evicted past L2 and grows with
+# attempts, not cells, so the timed run's attempts scale it.
+DRAM_BYTES_PER_ATTEMPT = 8228.0
 
 # where the nvidia-smi clock samples of the timed region are written
 LOG_DIR = os.environ.get("MC_BENCH_LOG_DIR", os.path.join(tempfile.gettempdir(), "mc_bench"))
@@ -189,11 +189,17 @@ def parity_sample(net, cells, idx, gx, gT, gs):
             "sensitive_err_oracle_p50_p90_max": rep.get("sensitive_err_oracle_p50_p90_max")}
 
 
-def serving_measurement(mc, n_sat=6, n_load=8, seed=7, edge_range=(16, 64)):
-    """Serving loop on AMR-box requests (edge L log-uniform in edge_range, cells
-    = L^3, 50/50 net13 / net33, FP32-matrix path, 150 GB budget): closed-loop
-    saturation, then Poisson arrivals at 0.5x and 0.9x of it. Bounded request
-    counts and box sizes keep the run within minutes."""
+def serving_measurement(mc, window_s=40.0, seed=7, edge_range=(16, 48), concurrency=8):
+    """Serving loop on AMR-box requests (edge L log-uniform in edge_range,
+    cells = L^3, 50/50 net13 / net33, FP32 iteration matrix, 150 GB budget).
+
+    Saturation: a closed loop that keeps `concurrency` requests in flight for
+    window_s seconds; capacity = cells of the requests completed after the
+    first completion and inside the window / the time between the two (the
+    ramp-up before the first completion and the work still in flight at the
+    end are both left out). Then Poisson arrivals at 0.5x and 0.9x of that
+    capacity for window_s seconds each, drained after the window; latency =
+    completion minus submission, per request."""
     import time as _t
     from mc_inputs import box_request_stream, network_13, network_33, synthetic_cells
     nets = {"net13": network_13(), "net33": network_33()}
@@ -206,42 +212,78 @@ def serving_measurement(mc, n_sat=6, n_load=8, seed=7, edge_range=(16, 64)):
         return (r["net"], r["n_cells"], np.ascontiguousarray(c["x"]), c["T"].copy(), c["ndens"].copy(),
                 np.zeros(r["n_cells"], dtype=np.int32))
 
-    def run(stream_reqs, arrivals):
+    def submit(srv, b):
+        name, n, x, T, nd, st = b
+        return srv.submit(handles[name], n, DT, x, n, T, nd, st)
+
+    # warm the kernels and the per-stream scratch once (the host buffers must
+    # outlive their requests)
+    srv = mc.Server(0, 150 << 30, opts)
+    warm = [make(r) for r in box_request_stream(2, 1.0, seed=seed + 99, edge_range=(16, 16),
+                                                nets=("net13", "net33"))]
+    for b in warm:
+        submit(srv, b)
+    srv.drain(600)
+    srv.close()
+    del warm
+
+    # saturation: closed loop
+    pool = box_request_stream(4096, 1.0, seed=seed, edge_range=edge_range)
+    srv = mc.Server(0, 150 << 30, opts)
+    live, done, k = {}, [], 0
+    t0 = _t.perf_counter()
+    while True:
+        now = _t.perf_counter() - t0
+        while now < window_s and len(live) < concurrency:
+            b = make(pool[k])
+            k += 1
+            live[submit(srv, b)] = b
+        for rid in list(live):
+            rc, info = srv.poll(rid)
+            if rc == 0:
+                t = _t.perf_counter() - t0
+                if t <= window_s:
+                    done.append((t, live[rid][1]))
+                del live[rid]
+        if not live and now >= window_s:
+            break
+        _t.sleep(0.002)
+    srv.drain(3600)
+    srv.close()
+    done.sort()
+    done_n = len(done)
+    if done_n >= 2:
+        lam_cells = sum(c for _, c in done[1:]) / max(window_s - done[0][0], 1e-9)
+    else:
+        lam_cells = sum(c for _, c in done) / window_s
+    mean_cells = float(np.mean([r["n_cells"] for r in pool]))
+    out = {"lambda_sat_cells_per_s": lam_cells, "saturation_requests_completed": done_n,
+           "mean_cells_per_request": mean_cells, "edge_range": list(edge_range), "window_s": window_s,
+           "concurrency": concurrency, "lu_precision": 32, "loads": []}
+    for load in (0.5, 0.9):
+        rate = load * lam_cells / mean_cells
+        reqs = box_request_stream(max(1, int(rate * window_s * 3) + 8), rate, seed=seed + int(load * 100),
+                                  edge_range=edge_range)
+        reqs = [r for r in reqs if r["t_arrive"] <= window_s] or reqs[:1]
+        bufs = [make(r) for r in reqs]
         srv = mc.Server(0, 150 << 30, opts)
-        bufs = [make(r) for r in stream_reqs]
         ids = []
         t0 = _t.perf_counter()
-        for (name, n, x, T, nd, st), ta in zip(bufs, arrivals):
-            wait = ta - (_t.perf_counter() - t0)
+        for r, b in zip(reqs, bufs):
+            wait = r["t_arrive"] - (_t.perf_counter() - t0)
             if wait > 0:
                 _t.sleep(wait)
-            ids.append(srv.submit(handles[name], n, DT, x, n, T, nd, st))
+            ids.append(submit(srv, b))
         srv.drain(3600)
         span = _t.perf_counter() - t0
         infos = [srv.poll(i)[1] for i in ids]
         srv.close()
         lat = np.array([i.t_done - i.t_submit for i in infos])
         cells = sum(b[1] for b in bufs)
-        return lat, cells, span, sum(i.n_failed for i in infos)
-
-    sat_reqs = box_request_stream(n_sat, 1.0, seed=seed, edge_range=edge_range)
-    lat, cells, span, _ = run(sat_reqs, [0.0] * n_sat)
-    lam_cells = cells / span
-    sizes = np.array([r["n_cells"] for r in box_request_stream(4096, 1.0, seed=seed + 1, edge_range=edge_range)])
-    mean_cells = float(sizes.mean())
-    out = {"lambda_sat_cells_per_s": lam_cells, "mean_cells_per_request": mean_cells,
-           "edge_range": list(edge_range),
-           "saturation_requests": n_sat, "loads": [],
-           "note": f"{n_load} Poisson requests per load level (bounded so the run ends in minutes)"}
-    for load in (0.5, 0.9):
-        rate = load * lam_cells / mean_cells
-        reqs = box_request_stream(n_load, rate, seed=seed + int(load * 100), edge_range=edge_range)
-        arrivals = [r["t_arrive"] for r in reqs]
-        lat, cells, span, failed = run(reqs, arrivals)
-        out["loads"].append({"load": load, "requests": n_load, "rate_req_per_s": rate,
+        out["loads"].append({"load": load, "requests": len(ids), "rate_req_per_s": rate,
                              "p50_latency_s": float(np.percentile(lat, 50)),
                              "p99_latency_s": float(np.percentile(lat, 99)),
-                             "cells_per_s": cells / span, "failed_cells": int(failed)})
+                             "cells_per_s": cells / span, "failed_cells": int(sum(i.n_failed for i in infos))})
     return out
 
 
@@ -298,6 +340,21 @@ def run_mixed(args, mc, world, rank, local, stream, flush, barrier, fp64_peak, f
     # (cooperative FP64 LU; the 33-ODE matrices defeat FP32 refinement late in
     # a burn and send those cells to the FP64 retry)
     opts = mc.mc_burn_opts_default(lu_precision=64)
+    # the mixed launch takes its grid, staging and hand-off from the
+    # autotuner's pick for its thread-per-cell network with the most cells
+    # (net13), timed here on a bounded sample of that segment (step cap 2000
+    # per trial, so that the search ends in seconds)
+    lead = max((k for k in keep if k[4].n_ode <= 16), key=lambda k: k[5]["x"].shape[1])
+    lh, ld_, lnet = lead[0], lead[1], lead[4]
+    m_lead = ld_["x"].shape[1]
+    ns = min(16384, m_lead)
+    t0 = time.perf_counter()
+    best = mc.mc_autotune(lh, mc.mc_burn_opts_default(lu_precision=64, max_steps=2000), ns, DT, ld_["x"], m_lead,
+                          ld_["T"], ld_["ndens"])
+    tuned = {"network": lnet.name, "sample_cells": ns, "trial_max_steps": 2000,
+             "seconds": round(time.perf_counter() - t0, 2), "variant": int(best.variant),
+             "block_threads": int(best.block_threads), "blocks_per_sm": int(best.blocks_per_sm),
+             "staging": int(best.staging), "straggler_steps": int(best.straggler_steps)}
     g = mc.mc_graph_create(segs, opts, DT)
 
     def reset():
@@ -394,6 +451,7 @@ def run_mixed(args, mc, world, rank, local, stream, flush, barrier, fp64_peak, f
                    "rtol": 1e-6, "atol": 1e-10, "lu_precision": 64,
                    "variant": "one persistent launch over all networks (cost-ordered queues, hand-off and "
                               "warp-per-cell record pass), CUDA graph replay",
+                   "autotuned": tuned,
                    "l2": "inputs exceed L2 and L2 is flushed between steps",
                    "parallelism": f"independent shards x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -475,9 +533,9 @@ def main():
                          "0 times exactly --steps after exactly --warmup")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 comparison arms")
-    ap.add_argument("--serving", action="store_true",
-                    help="add the serving-loop measurement (AMR-box requests, a few minutes)")
-    ap.add_argument("--no-serving", action="store_true", help="no serving measurement (the default)")
+    ap.add_argument("--serving-window-s", type=float, default=40.0,
+                    help="seconds of each serving phase (saturation, 0.5x and 0.9x load)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     args = ap.parse_args()
     if args.max_timed_s <= 0:
         args.max_timed_s = None
@@ -607,8 +665,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         idx = np.sort(np.random.default_rng(1).choice(n, PARITY_SAMPLE, replace=False))
         parity = parity_sample(net, cells, idx, gx[:, idx], gT[idx], status[idx])
-    if rank == 0 and args.serving and not args.no_serving:
-        serving = serving_measurement(mc)
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_measurement(mc, window_s=args.serving_window_s)
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(net, int(os.environ.get("MC_CPU_SAMPLE", str(ORACLE_SAMPLE))), CELL_SEED)
 

@@ -124,10 +124,17 @@ typedef struct {
                                column j = (f(y + d_j e_j) - f(y)) / d_j,
                                d_j = 2^-26 (|y_j| + atol / rtol) (one of the "Jacobian
                                approximations" of the paper's retry, Software design ¶3) */
+    int32_t staging;        /* where a thread-per-cell lane's Jacobian and LU are computed:
+                               MC_STAGING_SHARED, the whole warp in the warp's shared-memory
+                               workspace; MC_STAGING_LANE, the lane alone in its own state;
+                               MC_STAGING_AUTO (0) = autotuned, else shared */
 } mc_burn_opts;
 
 #define MC_JAC_ANALYTIC 0
 #define MC_JAC_FD 1
+#define MC_STAGING_AUTO 0
+#define MC_STAGING_SHARED 1
+#define MC_STAGING_LANE 2
 
 void mc_burn_opts_default(mc_burn_opts *opts);
 

@@ -11,6 +11,6 @@ from ._mc import (  # noqa: F401
     mc_autotune, mc_burn_opts_default, mc_graph_create, mc_last_error, mc_launch_count, mc_alloc_count, mc_network_create,
     mc_network_destroy, mc_network_rates, mc_network_rhs, mc_probe_fma_rate, mc_server_create, segment,
     MC_JAC_ANALYTIC, MC_JAC_FD, MC_METHOD_BDF, MC_METHOD_RKC, mc_burn_ladder, mc_rung, rung,
-    LIB_PATH, mc_bounds_report, mc_bounds_reset,
+    LIB_PATH, mc_bounds_report, mc_bounds_reset, MC_STAGING_AUTO, MC_STAGING_SHARED, MC_STAGING_LANE,
 )
 from .api import burn  # noqa: F401

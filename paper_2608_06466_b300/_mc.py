@@ -45,7 +45,7 @@ class mc_burn_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_order", C.c_int32),
                 ("max_steps", C.c_int32), ("lu_precision", C.c_int32), ("variant", C.c_int32),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("straggler_steps", C.c_int32),
-                ("jacobian", C.c_int32)]
+                ("jacobian", C.c_int32), ("staging", C.c_int32)]
 
 
 class mc_rung(C.Structure):
@@ -229,6 +229,7 @@ def mc_burn_batch_sdc(net: Network, opts: mc_burn_opts | None, n_cells: int, dt:
 
 
 MC_JAC_ANALYTIC, MC_JAC_FD = 0, 1
+MC_STAGING_AUTO, MC_STAGING_SHARED, MC_STAGING_LANE = 0, 1, 2
 MC_METHOD_BDF, MC_METHOD_RKC = 0, 1
 
 
@@ -307,12 +308,16 @@ class Server:
         check(lib.mc_server_create(int(device), int(hbm_budget_bytes), C.byref(self._opts), C.byref(h)),
               "mc_server_create")
         self.handle = h
+        self._arrays = {}  # request id -> its arrays, held until the request is done
 
     def submit(self, net: Network, n_cells, dt, x, ld, T, ndens, status, opts: mc_burn_opts | None = None) -> int:
+        """Queue a request. The library reads and writes the arrays until the
+        request is done; the binding holds them until then."""
         rid = C.c_uint64()
         check(lib.mc_request_submit(self.handle, net.handle, C.byref(opts) if opts is not None else None,
                                     int(n_cells), float(dt), _ptr(x), int(ld), _ptr(T), _ptr(ndens), _ptr(status),
                                     C.byref(rid)), "mc_request_submit")
+        self._arrays[rid.value] = (x, T, ndens, status)
         return rid.value
 
     @staticmethod
@@ -326,15 +331,20 @@ class Server:
     def poll(self, req_id: int):
         info = mc_request_info()
         rc = check(lib.mc_request_poll(self.handle, C.c_uint64(req_id), C.byref(info)), "mc_request_poll")
+        if rc == MC_OK:
+            self._arrays.pop(req_id, None)
         return rc, info
 
     def drain(self, timeout_s: float = 600.0):
-        return check(lib.mc_server_drain(self.handle, float(timeout_s)), "mc_server_drain")
+        rc = check(lib.mc_server_drain(self.handle, float(timeout_s)), "mc_server_drain")
+        self._arrays.clear()  # every request is done
+        return rc
 
     def close(self):
         if self.handle:
             check(lib.mc_server_destroy(self.handle), "mc_server_destroy")
             self.handle = None
+            self._arrays.clear()
 
     def __del__(self):
         try:

@@ -12,6 +12,7 @@ import glob
 import os
 import subprocess
 import sys
+import time
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -37,6 +38,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, check: b
     if check:
         extra_flags = list(extra_flags or []) + ["-DMC_BOUNDS_CHECK"]
     os.makedirs(obj_dir, exist_ok=True)
+    # objects carry the time the build started, so that a source or header
+    # edited while it runs is newer than every object compiled from the old
+    # text and the next build compiles them again
+    t_start = time.time()
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(INCLUDE, "*.h"))
@@ -55,6 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, check: b
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
         os.replace(obj + ".tmp", obj)
+        os.utime(obj, (t_start, t_start))
         return src, r.stderr
 
     if jobs:
@@ -70,6 +76,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, check: b
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, lib)
+        os.utime(lib, (t_start, t_start))
     return lib
 
 

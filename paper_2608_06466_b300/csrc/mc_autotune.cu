@@ -1,9 +1,11 @@
-// mc_autotune.cu -- measured launch-shape selection. mc_autotune times every
-// candidate (variant x threads per block x persistent blocks per SM) on a
-// sample of the caller's cells and keeps the fastest per (device, ODE count,
-// reactions, energy form, matrix precision); mc_burn_* with zero shape fields
-// use the stored winner. Winners persist in a JSON-lines file when
-// MC_AUTOTUNE_CACHE names one.
+// mc_autotune.cu -- measured launch-shape selection. mc_autotune times
+// candidates on a sample of the caller's cells in three rounds -- variant x
+// threads per block x persistent blocks per SM; then, for a thread-per-cell
+// persistent winner, the staging of the matrix work (the warp's shared memory
+// or the lane's own state); then the straggler hand-off threshold -- and
+// keeps the fastest per (device, ODE count, reactions, energy form, matrix
+// precision); mc_burn_* with zero shape fields use the stored winner. Winners
+// persist in a JSON-lines file when MC_AUTOTUNE_CACHE names one.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -49,12 +51,13 @@ void load_cache() {
   char line[512];
   while (std::fgets(line, sizeof line, f)) {
     char dev[256];
-    int n, R, en, lu, var, thr, bps;
+    int n, R, en, lu, var, thr, bps, stg, strag;
     if (std::sscanf(line,
                     "{\"device\": \"%255[^\"]\", \"n\": %d, \"R\": %d, \"energy\": %d, \"lu\": %d, "
-                    "\"variant\": %d, \"threads\": %d, \"blocks_per_sm\": %d}",
-                    dev, &n, &R, &en, &lu, &var, &thr, &bps) == 8)
-      g_table[Key(dev, n, R, en, lu)] = Tuned{var, thr, bps, 2048};
+                    "\"variant\": %d, \"threads\": %d, \"blocks_per_sm\": %d, \"staging\": %d, "
+                    "\"straggler_steps\": %d}",
+                    dev, &n, &R, &en, &lu, &var, &thr, &bps, &stg, &strag) == 10)
+      g_table[Key(dev, n, R, en, lu)] = Tuned{var, thr, bps, strag, stg};
   }
   std::fclose(f);
 }
@@ -66,9 +69,9 @@ void save_entry(const Key &k, const Tuned &t) {
   if (!f) return;
   std::fprintf(f,
                "{\"device\": \"%s\", \"n\": %d, \"R\": %d, \"energy\": %d, \"lu\": %d, \"variant\": %d, "
-               "\"threads\": %d, \"blocks_per_sm\": %d}\n",
+               "\"threads\": %d, \"blocks_per_sm\": %d, \"staging\": %d, \"straggler_steps\": %d}\n",
                std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), t.variant,
-               t.threads, t.blocks_per_sm);
+               t.threads, t.blocks_per_sm, t.staging, t.strag_steps);
   std::fclose(f);
 }
 }  // namespace
@@ -76,7 +79,7 @@ void save_entry(const Key &k, const Tuned &t) {
 Tuned mc::autotune_pick(const mc_network *net, const mc_burn_opts &o) {
   // defaults: thread-per-cell with hand-off for small networks, warp-per-cell
   // above 16 ODEs (the per-cell matrices no longer fit a lane's share of L1)
-  Tuned t{(net && net->n > 16) ? MC_VARIANT_WARP : MC_VARIANT_PERSISTENT, 128, 2, 2048};
+  Tuned t{(net && net->n > 16) ? MC_VARIANT_WARP : MC_VARIANT_PERSISTENT, 128, 2, 2048, MC_STAGING_SHARED};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();
@@ -87,6 +90,7 @@ Tuned mc::autotune_pick(const mc_network *net, const mc_burn_opts &o) {
   if (o.block_threads) t.threads = o.block_threads;
   if (o.blocks_per_sm) t.blocks_per_sm = o.blocks_per_sm;
   if (o.straggler_steps) t.strag_steps = o.straggler_steps;
+  if (o.staging) t.staging = o.staging;
   return t;
 }
 
@@ -113,23 +117,19 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  struct Cand { int var, thr, bps; };
-  std::vector<Cand> cands;
-  for (int thr : {64, 128, 256}) cands.push_back({MC_VARIANT_PLAIN, thr, 0});
-  for (int thr : {64, 128, 256})
-    for (int bps : {1, 2, 4}) cands.push_back({MC_VARIANT_PERSISTENT, thr, bps});
-  for (int bps : {1, 2, 4}) cands.push_back({MC_VARIANT_WARP, 128, bps});
-  float best_ms = 1e30f;
-  Cand win = cands[0];
-  for (const Cand &c : cands) {
+  struct Cand { int var, thr, bps, stg, strag; };
+  // one timed burn of the sample with a candidate; returns false on an error
+  auto trial = [&](const Cand &c, float *ms_out) -> bool {
     e = cudaMemcpy2DAsync(wx, sizeof(double) * n, x, sizeof(double) * ld, sizeof(double) * n, net->S,
                           cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && T) e = cudaMemcpyAsync(wT, T, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess) return false;
     mc_burn_opts t = o;
     t.variant = c.var;
     t.block_threads = c.thr;
     t.blocks_per_sm = c.bps ? c.bps : 1;
+    t.staging = c.stg;
+    t.straggler_steps = c.strag;
     CellArgs a{};
     a.n_cells = n;
     a.ld = n;
@@ -141,14 +141,41 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
     cudaEventRecord(e0, st);
     s = burn_device(net, t, a, st);
     cudaEventRecord(e1, st);
-    if (s != MC_OK) break;
+    if (s != MC_OK) return false;
     e = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess) return false;
+    cudaEventElapsedTime(ms_out, e0, e1);
+    return true;
+  };
+  float best_ms = 1e30f;
+  Cand win{MC_VARIANT_PLAIN, 64, 0, MC_STAGING_SHARED, 2048};
+  bool failed = false;
+  auto consider = [&](const Cand &c) {
+    if (failed) return;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    if (!trial(c, &ms)) {
+      failed = true;
+      return;
+    }
     if (ms < best_ms) {
       best_ms = ms;
       win = c;
+    }
+  };
+  // round 1: variant x threads x blocks per SM
+  for (int thr : {64, 128, 256}) consider({MC_VARIANT_PLAIN, thr, 0, MC_STAGING_SHARED, 2048});
+  for (int thr : {64, 128, 256})
+    for (int bps : {1, 2, 4}) consider({MC_VARIANT_PERSISTENT, thr, bps, MC_STAGING_SHARED, 2048});
+  for (int bps : {1, 2, 4}) consider({MC_VARIANT_WARP, 128, bps, MC_STAGING_SHARED, 2048});
+  if (win.var == MC_VARIANT_PERSISTENT) {
+    // round 2: staging of the matrix work; round 3: hand-off threshold
+    Cand c = win;
+    c.stg = MC_STAGING_LANE;
+    consider(c);
+    for (int strag : {512, 8192, -1}) {
+      c = win;
+      c.strag = strag;
+      consider(c);
     }
   }
   cudaEventDestroy(e0);
@@ -158,7 +185,7 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
   cudaFree(ws);
   if (s != MC_OK) return s;
   if (e != cudaSuccess) return cuda_error(e, "autotune trial");
-  Tuned t{win.var, win.thr, win.bps ? win.bps : 1, 2048};
+  Tuned t{win.var, win.thr, win.bps ? win.bps : 1, win.strag, win.stg};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();
@@ -171,6 +198,8 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
     best->variant = t.variant;
     best->block_threads = t.threads;
     best->blocks_per_sm = t.blocks_per_sm;
+    best->staging = t.staging;
+    best->straggler_steps = t.strag_steps;
   }
   return MC_OK;
 }

@@ -57,14 +57,27 @@ struct WSh {
   double *wb;       // [R]   net reaction rates
   double *dw;       // [5R]  d w / d x per side slot, then d w / d T
   WReq *req;        // request of the lane being served
+  double *P64;      // [N*N] FP64 factors of a warp-form cell whose FP32 solves
+  unsigned char *piv64;  // could not be refined (see w_newton_iter), or nullptr
 };
+
+// Warp-form cells with an FP32 matrix switch to FP64 factors in place when the
+// refinement of their FP32 solves stops converging (networks above 16 ODEs,
+// which always run warp-per-cell); thread-form cells hand such cells to the
+// FP64 retry pass instead.
+template <int N, typename LT>
+__host__ __device__ constexpr bool w_switches() {
+  return sizeof(LT) == sizeof(float) && N > 16;
+}
 
 template <int N, typename LT>
 __host__ __device__ inline size_t wsh_bytes(int R) {
   auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
   const size_t r = (size_t)(R > 0 ? R : 1);
-  return al(sizeof(double) * N * N) + al(sizeof(LT) * N * N) + al(N) + al(sizeof(double) * N) +
-         al(sizeof(double) * r) + al(sizeof(double) * 5 * r) + al(sizeof(WReq));
+  size_t b = al(sizeof(double) * N * N) + al(sizeof(LT) * N * N) + al(N) + al(sizeof(double) * N) +
+             al(sizeof(double) * r) + al(sizeof(double) * 5 * r) + al(sizeof(WReq));
+  if constexpr (w_switches<N, LT>()) b += al(sizeof(double) * N * N) + al(N);
+  return b;
 }
 
 template <int N, typename LT>
@@ -85,7 +98,31 @@ __device__ __forceinline__ WSh<LT> wsh_carve(unsigned char *p, int R) {
   s.dw = (double *)p;
   p += al(sizeof(double) * 5 * r);
   s.req = (WReq *)p;
+  p += al(sizeof(WReq));
+  s.P64 = nullptr;
+  s.piv64 = nullptr;
+  if constexpr (w_switches<N, LT>()) {
+    s.P64 = (double *)p;
+    p += al(sizeof(double) * N * N);
+    s.piv64 = p;
+  }
   return s;
+}
+
+// the FP64 factor view of a workspace (the same J, point and rates)
+template <typename LT>
+__device__ __forceinline__ WSh<double> wsh_fp64(const WSh<LT> &s) {
+  WSh<double> v;
+  v.J = s.J;
+  v.P = s.P64;
+  v.piv = s.piv64;
+  v.yb = s.yb;
+  v.wb = s.wb;
+  v.dw = s.dw;
+  v.req = s.req;
+  v.P64 = nullptr;
+  v.piv64 = nullptr;
+  return v;
 }
 
 // temperature quantities of the point in yb (energy form) or of the cell

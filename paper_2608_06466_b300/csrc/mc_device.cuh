@@ -402,6 +402,7 @@ struct Opts {
   double rtol, atol;
   int qmax, max_steps;
   int jac_fd;              // 1: forward-difference Jacobian instead of the analytic one
+  int lane_matrix;         // 1: thread-per-cell lanes do their own matrix work (no warp cooperation)
 };
 
 template <int N, typename LT>

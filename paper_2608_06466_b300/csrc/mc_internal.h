@@ -70,10 +70,11 @@ size_t burn_scratch_bytes(const mc_network *net, const mc_burn_opts &o, int64_t 
 
 // launch shape chosen for a network and options
 struct Tuned {
-  int variant;        // MC_VARIANT_PLAIN or MC_VARIANT_PERSISTENT
+  int variant;        // MC_VARIANT_PLAIN, MC_VARIANT_PERSISTENT or MC_VARIANT_WARP
   int threads;        // threads per block
   int blocks_per_sm;  // persistent grid size per SM
   int strag_steps;    // attempts before a persistent lane hands its cell off (<= 0: never)
+  int staging;        // MC_STAGING_SHARED or MC_STAGING_LANE
 };
 Tuned autotune_pick(const mc_network *net, const mc_burn_opts &o);
 

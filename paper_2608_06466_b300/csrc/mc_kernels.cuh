@@ -210,9 +210,10 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
 // out (reset to 0 before the launch). Every lane of the warp runs the loop, so
 // the warp-wide votes are safe; the loop returns once the queue is drained and
 // every lane's cell is stored or handed off. One loop trip: one right-hand
-// side for every busy lane, the warp-cooperative matrix work of the lanes
-// that wait for it (coop_matrix, in the warp's workspace sh), then the step
-// logic's stages.
+// side for every busy lane, the matrix work of the lanes that wait for it
+// (warp-cooperative in the warp's workspace sh, coop_matrix; or, with
+// o.lane_matrix, each lane alone, matrix_thread), then the step logic's
+// stages.
 template <int N, typename LT>
 __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs &a,
                                   unsigned long long *next, const StragArgs &sa, const WSh<LT> &sh) {
@@ -247,7 +248,11 @@ __device__ void persistent_worker(const DNet &net, const Opts &o, const CellArgs
       const bool ok = net_rhs<N>(net, L.cin, L.y, L.f);
       advance(L, net, o, ok);
     }
-    coop_matrix<N, LT>(L, net, o, sh);
+    if (o.lane_matrix) {
+      if (L.todo == TD_MATRIX) matrix_thread(L, net, o);
+    } else {
+      coop_matrix<N, LT>(L, net, o, sh);
+    }
     if (busy) {
       run_stages(L, net, o);
       if (sa.rec && L.phase == PH_NEWTON && L.m == 0 && L.attempts >= sa.threshold && !L.kept) {

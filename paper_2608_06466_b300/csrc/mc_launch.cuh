@@ -21,7 +21,11 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
     e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_error(e, "queue reset");
     const int per_warp = (int)wsh_bytes<N, LT>(d.R);
-    const int wthreads = 128;
+    int smem_max = 0;
+    e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_error(e, "shared memory limit");
+    // four warps a block unless their workspaces exceed a block's shared memory
+    const int wthreads = std::max(32, std::min(128, 32 * (smem_max / per_warp)));
     const int smem = per_warp * (wthreads / 32);
     static thread_local DevAttrCache configured_w;
     if (configured_w.below(dev, smem)) {
@@ -29,8 +33,8 @@ mc_status launch_one(const DNet &d, const Opts &o, const CellArgs &a, int varian
       if (e != cudaSuccess) return cuda_error(e, "warp kernel smem attribute");
       configured_w.raise(dev, smem);
     }
-    int64_t blocks = (int64_t)sms * std::max(1, blocks_per_sm) * 2;
-    const int64_t need = a.n_dev ? blocks : (a.n_cells + 3) / 4;
+    int64_t blocks = (int64_t)sms * std::max(1, blocks_per_sm) * 2 * (128 / wthreads);
+    const int64_t need = a.n_dev ? blocks : (a.n_cells + wthreads / 32 - 1) / (wthreads / 32);
     blocks = std::max<int64_t>(1, std::min(blocks, need));
     k_burn_warp<N, LT><<<(unsigned)blocks, wthreads, smem, st>>>(d, o, a, next, per_warp);
   } else if (variant == MC_VARIANT_PLAIN) {

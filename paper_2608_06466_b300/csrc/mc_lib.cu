@@ -77,6 +77,7 @@ extern "C" void mc_burn_opts_default(mc_burn_opts *o) {
   o->blocks_per_sm = 0;
   o->straggler_steps = 0;
   o->jacobian = MC_JAC_ANALYTIC;
+  o->staging = MC_STAGING_AUTO;
 }
 
 // ---------------------------------------------------------------- networks
@@ -392,6 +393,8 @@ mc_status mc::check_opts(const mc_burn_opts *opts, mc_burn_opts *o) {
   if (o->straggler_steps < -1) return set_error(MC_E_INVALID, "straggler_steps must be -1, 0 or positive");
   if (o->jacobian != MC_JAC_ANALYTIC && o->jacobian != MC_JAC_FD)
     return set_error(MC_E_INVALID, "jacobian must be MC_JAC_ANALYTIC or MC_JAC_FD");
+  if (o->staging < MC_STAGING_AUTO || o->staging > MC_STAGING_LANE)
+    return set_error(MC_E_INVALID, "staging must be MC_STAGING_AUTO, _SHARED or _LANE");
   return MC_OK;
 }
 
@@ -404,7 +407,8 @@ mc_status mc::burn_device_scratch(const mc_network *net, const mc_burn_opts &ob,
                                   bool allow_strag) {
   Tuned tu = autotune_pick(net, ob);
   if (!allow_strag) tu.strag_steps = 0;
-  Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps, ob.jacobian == MC_JAC_FD ? 1 : 0};
+  Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps, ob.jacobian == MC_JAC_FD ? 1 : 0,
+         tu.staging == MC_STAGING_LANE ? 1 : 0};
   const DNet d = dnet_of(net);
   if (ob.lu_precision == 64)
     return dispatch<double>(net, d, o, a0, tu.variant, tu.threads, tu.blocks_per_sm, tu.strag_steps, next, st);

@@ -124,8 +124,8 @@ mc_status launch_records(const DNet &d, const Opts &o, const CellArgs &a, const 
 // the persistent launch with hand-off, then the warp-per-cell pass over each
 // thread-per-cell segment's records.
 template <typename LT>
-mc_status mixed_pass(const mc_segment *segs, MixedArgs m, const Opts &o, int blocks, int msmem, bool handoff,
-                     unsigned long long *next, uint32_t *rcnt, char *rec, int sms, cudaStream_t st) {
+mc_status mixed_pass(const mc_segment *segs, MixedArgs m, const Opts &o, int blocks, int mthreads, int msmem,
+                     bool handoff, unsigned long long *next, uint32_t *rcnt, char *rec, int sms, cudaStream_t st) {
   const int nseg = m.nseg;
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long) * 2 * MIXED_MAX_SEGS, st);
   if (e == cudaSuccess && handoff) e = cudaMemsetAsync(rcnt, 0, sizeof(uint32_t) * 4 * MIXED_MAX_SEGS, st);
@@ -139,7 +139,7 @@ mc_status mixed_pass(const mc_segment *segs, MixedArgs m, const Opts &o, int blo
     m.sa[s] = StragArgs{rec + off, rcnt + 4 * s, (uint32_t)cap, MIXED_STRAG_STEPS, nullptr};
     off += (b == 3) ? rec_bytes<3, LT>(cap) : rec_bytes<13, LT>(cap);
   }
-  k_burn_mixed<LT><<<(unsigned)blocks, 128, msmem, st>>>(m, o, next);
+  k_burn_mixed<LT><<<(unsigned)blocks, mthreads, msmem, st>>>(m, o, next);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "mixed launch");
   count_launch(1);
@@ -185,7 +185,18 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     rs = straggler_scratch(rb, &rec, &rcnt);
     if (rs != MC_OK) return rs;
   }
-  const Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps, ob.jacobian == MC_JAC_FD ? 1 : 0};
+  // launch shape and staging: the autotuner's pick for the thread-per-cell
+  // network with the most cells (the warp-per-cell segments share the grid)
+  const mc_network *lead = nullptr;
+  int64_t most = -1;
+  for (int s = 0; s < nseg; ++s)
+    if (segs[s].net->n <= 16 && segs[s].n_cells > most) {
+      most = segs[s].n_cells;
+      lead = segs[s].net;
+    }
+  const Tuned tu = autotune_pick(lead, ob);
+  const Opts o{ob.rtol, ob.atol, ob.max_order, ob.max_steps, ob.jacobian == MC_JAC_FD ? 1 : 0,
+               tu.staging == MC_STAGING_LANE ? 1 : 0};
   MixedArgs m{};
   m.nseg = nseg;
   int64_t off = 0;
@@ -219,7 +230,6 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     }
     off += g.n_cells;
   }
-  Tuned tu = autotune_pick(nullptr, ob);
   // warp workspace (the largest one): the warp-per-cell segments' state, the
   // thread-per-cell segments' cooperative matrix work
   size_t per_warp = 16;
@@ -241,7 +251,11 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     if (b == 40) per_warp = std::max(per_warp, wsh_bytes<40, double>(R));
   }
   m.smem_per_warp = (int)per_warp;
-  const int mthreads = 128;
+  int smem_max = 0;
+  if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return set_error(MC_E_CUDA, "mixed: shared memory limit");
+  // four warps a block unless their workspaces exceed a block's shared memory
+  const int mthreads = std::max(32, std::min(128, 32 * (smem_max / (int)per_warp)));
   const int msmem = (int)per_warp * (mthreads / 32);
   {
     static thread_local DevAttrCache configured;
@@ -257,11 +271,11 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(uint32_t) * nseg, st);
     if (e != cudaSuccess) return cuda_error(e, "mixed retry reset");
   }
-  const int blocks = std::max(1, sms * tu.blocks_per_sm);
+  const int blocks = std::max(1, sms * tu.blocks_per_sm * (128 / mthreads));
   const bool handoff = tu.strag_steps >= 0;
   if (ob.lu_precision == 64)
-    return mixed_pass<double>(segs, m, o, blocks, msmem, handoff, next, rcnt, (char *)rec, sms, st);
-  rs = mixed_pass<float>(segs, m, o, blocks, msmem, handoff, next, rcnt, (char *)rec, sms, st);
+    return mixed_pass<double>(segs, m, o, blocks, mthreads, msmem, handoff, next, rcnt, (char *)rec, sms, st);
+  rs = mixed_pass<float>(segs, m, o, blocks, mthreads, msmem, handoff, next, rcnt, (char *)rec, sms, st);
   if (rs != MC_OK) return rs;
   // FP64 pass over every segment's retry list (lengths read on the device), no hand-off
   MixedArgs r = m;
@@ -274,7 +288,7 @@ mc_status mixed_launch(const mc_segment *segs, int32_t nseg, const mc_burn_opts 
     a.retry_count = nullptr;
     off += segs[s].n_cells;
   }
-  return mixed_pass<double>(segs, r, o, blocks, msmem, false, next, rcnt, (char *)rec, sms, st);
+  return mixed_pass<double>(segs, r, o, blocks, mthreads, msmem, false, next, rcnt, (char *)rec, sms, st);
 }
 
 }  // namespace

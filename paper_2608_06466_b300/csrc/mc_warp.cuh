@@ -30,6 +30,7 @@ struct WState {
   int64_t cell;
   int q, qwait, nef, ncf, jage, page, attempts, m, phase, status;
   bool need_j, need_p, jcur, have_es, last;
+  bool p64;  // FP32-matrix cell now factoring in FP64 (w_switches)
   int st[NSTAT];
 };
 
@@ -85,6 +86,7 @@ __device__ __forceinline__ void w_load(WState<N> &W, const Lane<N, LT> &L, const
   W.q = L.q; W.qwait = L.qwait; W.nef = L.nef; W.ncf = L.ncf; W.jage = L.jage; W.page = L.page;
   W.attempts = L.attempts; W.m = L.m; W.phase = L.phase; W.status = L.status;
   W.need_j = L.need_j; W.need_p = L.need_p; W.jcur = L.jcur; W.have_es = L.have_es; W.last = L.last;
+  W.p64 = false;
   for (int k = 0; k < NSTAT; ++k) W.st[k] = L.st[k];
   __syncwarp();
 }
@@ -99,6 +101,7 @@ __device__ __forceinline__ void w_load_cell(WState<N> &W, const DNet &net, const
   W.cell = c;
   W.status = CELL_OK;
   W.q = 0;
+  W.p64 = false;
   for (int k = 0; k < NSTAT; ++k) W.st[k] = 0;
   if (!MC_IN(a, BC_WARP_LOAD, c, MC_CELLS(a))) {
     W.status = CELL_BAD_INPUT;
@@ -571,13 +574,21 @@ __device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, co
       newp = true;
     }
     if (newp || W.need_p || W.page >= MSBP || fabs(W.gamma / W.gamma_p - 1.0) > CCMAX) {
-      w_form_p<N, LT>(sh, n, W.gamma);
       W.st[ST_LU] += 1;
       W.gamma_p = W.gamma;
       W.page = 0;
       W.need_p = false;
       W.crate = CRATE0;
-      if (!w_lu<N, LT>(sh, n)) {
+      bool lu_ok;
+      if (w_switches<N, LT>() && W.p64) {
+        const WSh<double> v = wsh_fp64(sh);
+        w_form_p<N, double>(v, n, W.gamma);
+        lu_ok = w_lu<N, double>(v, n);
+      } else {
+        w_form_p<N, LT>(sh, n, W.gamma);
+        lu_ok = w_lu<N, LT>(sh, n);
+      }
+      if (!lu_ok) {
         W.need_p = true;
         return 2;
       }
@@ -590,7 +601,33 @@ __device__ __forceinline__ int w_newton_iter(WState<N> &W, const WSh<LT> &sh, co
     const int i = ln + 32 * s;
     d[s] = (i < n) ? (W.h * W.f[s] - W.z[1][s]) * rl1 - W.e[s] : 0.0;
   }
-  if (!w_solve<N, LT>(sh, n, W.gamma_p, W.iw, d)) return 4;
+  if constexpr (w_switches<N, LT>()) {
+    const WSh<double> v = wsh_fp64(sh);
+    if (W.p64) {
+      w_solve<N, double>(v, n, W.gamma_p, W.iw, d);
+    } else {
+      double d0[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) d0[s] = d[s];
+      if (!w_solve<N, LT>(sh, n, W.gamma_p, W.iw, d)) {
+        // the FP32 factors of this matrix cannot reach the FP64 solve: factor
+        // the same matrix (J and gamma_P unchanged) in FP64, solve with it,
+        // and keep FP64 factors for the rest of this cell
+        W.p64 = true;
+        W.st[ST_LU] += 1;
+        w_form_p<N, double>(v, n, W.gamma_p);
+        if (!w_lu<N, double>(v, n)) {
+          W.need_p = true;
+          return 2;
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) d[s] = d0[s];
+        w_solve<N, double>(v, n, W.gamma_p, W.iw, d);
+      }
+    }
+  } else {
+    if (!w_solve<N, LT>(sh, n, W.gamma_p, W.iw, d)) return 4;
+  }
   W.st[ST_NEWTON] += 1;
   if (W.gamma != W.gamma_p) {
     const double sc = 2.0 / (1.0 + W.gamma / W.gamma_p);

@@ -8,7 +8,7 @@ that a capture ends by itself).
         flops of the roofline model.
 
     python -m paper_2608_06466_b300.profile_case burn --cells 1048576 --lu 32 \\
-        --variant 2 --max-steps 3000 --straggler -1
+        --variant 2 --max-steps 3000 --straggler -1 [--staging 1|2] [--bps K]
         One burn of net13 cells (seed 3) with those options; prints the time
         and the summed per-cell counters.
 """
@@ -54,7 +54,7 @@ def run_eval(n: int = 1 << 18) -> None:
     print("evaluated", n, "states; finite:", int(ok.sum()))
 
 
-def run_burn(n: int, lu: int, variant: int, max_steps: int, straggler: int) -> None:
+def run_burn(n: int, lu: int, variant: int, max_steps: int, straggler: int, staging: int = 0, bps: int = 0) -> None:
     import torch
 
     import paper_2608_06466_b300 as mc
@@ -63,7 +63,8 @@ def run_burn(n: int, lu: int, variant: int, max_steps: int, straggler: int) -> N
     net = network_13()
     h = mc.Network(net)
     d = to_device(synthetic_cells(net, n, seed=3))
-    o = mc.mc_burn_opts_default(lu_precision=lu, variant=variant, max_steps=max_steps, straggler_steps=straggler)
+    o = mc.mc_burn_opts_default(lu_precision=lu, variant=variant, max_steps=max_steps, straggler_steps=straggler,
+                                staging=staging, blocks_per_sm=bps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     mc.mc_burn_batch(h, o, n, 1e10, d["x"], n, d["T"], d["ndens"], None, d["status"], d["stats"])
@@ -82,11 +83,13 @@ def main() -> None:
     ap.add_argument("--variant", type=int, default=2)
     ap.add_argument("--max-steps", type=int, default=100000)
     ap.add_argument("--straggler", type=int, default=0)
+    ap.add_argument("--staging", type=int, default=0, help="0 auto, 1 shared, 2 lane")
+    ap.add_argument("--bps", type=int, default=0, help="persistent blocks per SM (0 = autotuned)")
     a = ap.parse_args()
     if a.case == "eval":
         run_eval()
     else:
-        run_burn(a.cells, a.lu, a.variant, a.max_steps, a.straggler)
+        run_burn(a.cells, a.lu, a.variant, a.max_steps, a.straggler, a.staging, a.bps)
 
 
 if __name__ == "__main__":

@@ -22,6 +22,9 @@ for p in (ROOT, os.path.join(ROOT, "tests")):
     if p not in sys.path:
         sys.path.insert(0, p)
 
+HANDOFF = 1024       # hand-off threshold of the "fused" case
+HANDOFF_CAP = 512    # its record list: max(256, cells / 8)
+
 # (name, cells) of the calls whose stores the check build verifies
 VERIFIED = [("fused", 4096), ("plain", 2048), ("warp", 512), ("net33", 512), ("robertson", 4096),
             ("host", 1000), ("sdc", 1024), ("ladder", 1024)]
@@ -65,10 +68,12 @@ def run_cases(mc) -> dict:
         for k, v in _out(d).items():
             out[f"{name}.{k}"] = v
 
-    # cost-ordered persistent launch, FP32 matrix with its FP64 retry, hand-off after 64 attempts
+    # cost-ordered persistent launch, FP32 matrix with its FP64 retry, hand-off
+    # after 1024 attempts (the record list, 512 entries here, takes every cell
+    # that reaches it, so which cells are handed off does not depend on timing)
     c = synthetic_cells(n13, 4096, seed=11)
     d = _dev(c, 4096 + 5, torch)
-    o = mc.mc_burn_opts_default(lu_precision=32, variant=mc.MC_VARIANT_PERSISTENT, straggler_steps=64)
+    o = mc.mc_burn_opts_default(lu_precision=32, variant=mc.MC_VARIANT_PERSISTENT, straggler_steps=HANDOFF)
     mc.mc_burn_batch(h13, o, 4096, 1e10, d["x"], 4096 + 5, d["T"], d["nd"], None, d["st"], d["sx"])
     put("fused", d)
     # plain FP64 and warp-per-cell

@@ -47,6 +47,11 @@ def test_bounds_check_build_is_clean_and_matches(tmp_path):
     import paper_2608_06466_b300 as mc
     assert mc.mc_bounds_report(0)["enabled"] == 0  # the normal build checks nothing
     ref = bounds_case.run_cases(mc)
+    # bitwise equality needs a schedule-free hand-off: fewer cells reach the
+    # threshold than the record list holds (a full list leaves the choice of
+    # cells to timing, and thread and warp forms round differently)
+    sx = ref["fused.sx"][:, :4096].astype(np.int64)
+    assert int(((sx[0] + sx[1] + sx[2]) >= bounds_case.HANDOFF).sum()) < bounds_case.HANDOFF_CAP
     assert set(ref) == {k for k in chk if "." in k and not k.startswith("report.")}
     for k, v in ref.items():
         np.testing.assert_array_equal(chk[k], v, err_msg=k)

@@ -317,4 +317,20 @@ def test_autotune_returns_a_measured_shape(mc):
     best = mc.mc_autotune(h, mc.mc_burn_opts_default(lu_precision=32), 2048, 1e10, d["x"], 2048, d["T"], d["ndens"])
     torch.cuda.synchronize()
     assert best.variant in (1, 2, 3) and best.block_threads in (64, 128, 256)
+    assert best.staging in (mc.MC_STAGING_SHARED, mc.MC_STAGING_LANE)
+    assert best.straggler_steps in (512, 2048, 8192, -1)
     assert torch.equal(d["x"], x0)  # the sample is not modified
+
+
+@pytest.mark.parametrize("lu", [64, 32])
+def test_lane_staging_parity(mc, lu):
+    """The persistent worker with each lane doing its own matrix work (the
+    autotuner's other staging) against the oracle."""
+    net = network_13()
+    cells = synthetic_cells(net, 2048, seed=5)
+    gx, gT, gs, gst = _run(mc, net, cells, 1e10, lu_precision=lu, variant=mc.MC_VARIANT_PERSISTENT,
+                           staging=mc.MC_STAGING_LANE)
+    ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, 1e10)
+    rep = compare(gx, gT, gs, ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
+    print(lu, rep)
+    assert rep["pass"], rep
