@@ -437,14 +437,17 @@ struct Lane {
 // preconditioner, the residual r - (I - gamma_P J) d is formed in FP64 with the
 // FP64 Jacobian, and the correction is added in FP64. Sweeps stop once the
 // error-weighted max-norm of a correction is (or is predicted, from the
-// contraction of the last two, to be) below REFINE_TOL of the solution's,
-// when the corrections stop shrinking, or after REFINE_MAX sweeps (late in a
-// burn gamma J reaches 1e10 and cond(P) 1e12, where a sweep contracts the
-// error only by 0.05-0.2, so the cap leaves room for those). The Newton
-// correction then equals the FP64 solve's up to that share of a tolerance
-// unit, so the FP32 form takes the FP64 form's Newton iterates and decisions.
+// contraction of the last two, to be) below REFINE_TOL of the solution's or
+// below REFINE_ABS error-weight units outright, when the corrections stop
+// shrinking, or after REFINE_MAX sweeps (late in a burn gamma J reaches 1e10
+// and cond(P) 1e12, where a sweep contracts the error only by 0.05-0.2, so the
+// cap leaves room for those). The Newton correction then equals the FP64
+// solve's up to 1e-8 of a tolerance unit (Newton itself stops at about 0.1
+// of one), so the FP32 form takes the FP64 form's Newton iterates and
+// decisions.
 constexpr int REFINE_MAX = 24;
 constexpr float REFINE_TOL = 1e-10f;
+constexpr float REFINE_ABS = 1e-8f;
 
 // Newton correction: d <- (I - gamma_P J)^-1 d with the lane's factors.
 // Returns false when the FP32 factors cannot reproduce the FP64 solve (the
@@ -492,12 +495,13 @@ __device__ __forceinline__ bool newton_solve(const Lane<N, LT> &L, int n, double
 #pragma unroll
       for (int i = 0; i < N; ++i)
         if (i < n) nc = fmaxf(nc, fabsf(b[i]) * L.iw32[i]);
-      const bool done = nc <= REFINE_TOL * nd;
+      const float tol = fmaxf(REFINE_TOL * nd, REFINE_ABS);
+      const bool done = nc <= tol;
       if (!done && !(nc < np)) return false;  // no longer contracting
 #pragma unroll
       for (int i = 0; i < N; ++i)
         if (i < n) d[i] += (double)b[i];
-      if (done || nc * (nc / np) <= REFINE_TOL * nd) return true;
+      if (done || nc * (nc / np) <= tol) return true;
       np = nc;
     }
     return false;

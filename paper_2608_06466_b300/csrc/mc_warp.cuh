@@ -274,12 +274,13 @@ __device__ __forceinline__ bool w_solve(const WSh<LT> &sh, int n, double gamma_p
       for (int k = 0; k < NS; ++k)
         if (ln + 32 * k < n) nl = fmaxf(nl, fabsf(b[k]) * w[k]);
       const float nc = wmaxf(nl);
-      const bool done = nc <= REFINE_TOL * nd;
+      const float tol = fmaxf(REFINE_TOL * nd, REFINE_ABS);
+      const bool done = nc <= tol;
       if (!done && !(nc < np)) return false;  // no longer contracting
 #pragma unroll
       for (int k = 0; k < NS; ++k)
         if (ln + 32 * k < n) d[k] += (double)b[k];
-      if (done || nc * (nc / np) <= REFINE_TOL * nd) return true;
+      if (done || nc * (nc / np) <= tol) return true;
       np = nc;
     }
     return false;
