@@ -30,8 +30,10 @@
  * limit, the order of convergence, the starting step's closed form on linear
  * problems, the modified Newton correction (one exact correction on a linear
  * problem with a current matrix; the contraction factor of the scaled
- * correction with a matrix formed at another gamma), the Jacobian against
- * finite differences, and the LU against the definition.
+ * correction with a matrix formed at another gamma), the step-size rule's
+ * target (after a step change at order 1 the error estimates settle at
+ * 1/BIAS_q = 1/6; after an order raise at 1/BIAS_q+1 = 1/10), the Jacobian
+ * against finite differences, and the LU against the definition.
  *
  * Failure retry (same paragraph 3: retry a zone with different tolerances or
  * Jacobian approximations): a forward-difference Jacobian (pinned exact on a
@@ -47,12 +49,12 @@
  * constant source per cell and component added to the right-hand side
  * (pinned to straight lines, to a matrix exponential, to element totals).
  *
- * Parity unpinned: the step-control policy (the step-size factors
- * eta = 1/((BIAS E)^(1/(k+1)) + ADDON) and their bounds, when h and q may
- * change, the Newton convergence constants, the Jacobian/matrix reuse ages, the
- * failure ladders). These are heuristics with no closed form; they are checked
- * only through solution accuracy and through parity with the independent CUDA
- * implementation of the same rules.
+ * Parity unpinned: the rest of the step-control policy (the bounds of the
+ * step-size factors, when h and q may change, the Newton convergence
+ * constants, the Jacobian/matrix reuse ages, the failure ladders). These are
+ * heuristics with no closed form; they are checked only through solution
+ * accuracy and through parity with the independent CUDA implementation of the
+ * same rules.
  */
 #include <float.h>
 #include <math.h>
@@ -110,6 +112,9 @@ typedef struct {
     int max_order, max_steps;
     int jac_fd;        /* 1: forward-difference Jacobian instead of the analytic one */
     int method;        /* 0: BDF (the paper's VODE-style integrator), 1: RKC */
+    double *steplog;   /* optional record of accepted steps (the pins' view):      */
+    int steplog_cap;   /* (t after the step, h, q, error estimate) per step, at    */
+    int *steplog_n;    /* most steplog_cap of them; *steplog_n counts them         */
 } or_opts;
 
 static double harmonic(int k)
@@ -548,6 +553,14 @@ int or_bdf_integrate(const or_ode *ode, const or_opts *o, double t0, double t1, 
         for (int j = 0; j <= q; ++j)
             for (int i = 0; i < n; ++i) s->z[j * n + i] += l[j] * e[i];
         s->t = last ? t1 : s->t + s->h;
+        if (o->steplog && o->steplog_n && *o->steplog_n < o->steplog_cap) {
+            double *r = o->steplog + 4 * (*o->steplog_n);
+            r[0] = s->t;
+            r[1] = s->h;
+            r[2] = q;
+            r[3] = dsm;
+            *o->steplog_n += 1;
+        }
         for (int k = OR_QMAX + 2; k > 0; --k) s->hist[k] = s->hist[k - 1];
         s->hist[0] = s->h;
         st[ST_STEPS] += 1;
@@ -721,6 +734,24 @@ int or_linear_integrate(int n, const double *A, int deg, const double *c, double
     if (n < 1 || n > OR_NMAX || deg < 0 || deg > 7) return OR_BAD_INPUT;
     linear_ode(&p, n, A, deg, c, &ode);
     or_opts o = {rtol, atol, max_order, max_steps};
+    return or_bdf_integrate(&ode, &o, t0, t1, y, st);
+}
+
+/* or_linear_integrate with the record of accepted steps: steplog[4 k ..] =
+   (t after step k, h, q, error estimate) for k < *nlog <= cap. */
+int or_linear_integrate_steps(int n, const double *A, int deg, const double *c, double rtol,
+                              double atol, int max_order, int max_steps, double t0, double t1,
+                              double *y, int32_t *st, double *steplog, int cap, int *nlog)
+{
+    or_linear p;
+    or_ode ode;
+    if (n < 1 || n > OR_NMAX || deg < 0 || deg > 7) return OR_BAD_INPUT;
+    linear_ode(&p, n, A, deg, c, &ode);
+    or_opts o = {rtol, atol, max_order, max_steps};
+    *nlog = 0;
+    o.steplog = steplog;
+    o.steplog_cap = cap;
+    o.steplog_n = nlog;
     return or_bdf_integrate(&ode, &o, t0, t1, y, st);
 }
 

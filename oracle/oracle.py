@@ -75,6 +75,9 @@ def lib():
                                                C.c_int]
             L.or_linear_integrate.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_double,
                                               C.c_int, C.c_int, C.c_double, C.c_double, _dp, _ip]
+            L.or_linear_integrate_steps.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_double,
+                                                    C.c_int, C.c_int, C.c_double, C.c_double, _dp, _ip, _dp,
+                                                    C.c_int, _ip]
             L.or_linear_fixed_steps.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int, _dp,
                                                 C.c_double, _dp, _dp, _dp, _dp]
             L.or_linear_initial_step.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double]
@@ -257,6 +260,20 @@ def linear_integrate(A, c, y0, t0, t1, rtol=1e-6, atol=1e-10, max_order=5, max_s
     s = lib().or_linear_integrate(y.size, _d(A), c.shape[0] - 1, _d(c), rtol, atol, max_order,
                                   max_steps, t0, t1, _d(y), _i(st))
     return y, s, dict(zip(STAT_NAMES, st.tolist()))
+
+
+def linear_integrate_steps(A, c, y0, t0, t1, rtol=1e-6, atol=1e-10, max_order=5, max_steps=100000, cap=200000):
+    """linear_integrate with the record of accepted steps: rows (t after the
+    step, h, q, error estimate in the error-test norm)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    c = np.ascontiguousarray(np.atleast_2d(c), dtype=np.float64)
+    y = np.array(y0, dtype=np.float64)
+    st = np.zeros(NSTAT, dtype=np.int32)
+    log = np.zeros((cap, 4), dtype=np.float64)
+    nlog = np.zeros(1, dtype=np.int32)
+    s = lib().or_linear_integrate_steps(y.size, _d(A), c.shape[0] - 1, _d(c), rtol, atol, max_order,
+                                        max_steps, t0, t1, _d(y), _i(st), _d(log), cap, _i(nlog))
+    return y, s, dict(zip(STAT_NAMES, st.tolist())), log[:int(nlog[0])].copy()
 
 
 def linear_fixed_steps(A, c, q, hs, t0, z, hist):

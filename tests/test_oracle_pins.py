@@ -579,3 +579,51 @@ def test_stale_matrix_correction_contracts_at_its_closed_form_rate():
         assert res == 1 and tr.shape[0] == 3
         for k in range(3):
             assert abs(tr[k, 0] - e_star * (1 - rho ** (k + 1))) <= 1e-14 * abs(e_star)
+
+
+def _settled_estimate(log, k0, settle):
+    """Error estimates of the accepted steps from k0 + settle on, up to the
+    next step change (or the last step before the clipped final one)."""
+    h, E = log[:, 1], log[:, 3]
+    k1 = k0 + 1
+    while k1 < len(h) - 1 and abs(h[k1] / h[k0] - 1.0) < 1e-12:
+        k1 += 1
+    return E[k0 + settle:k1]
+
+
+def test_step_size_rule_targets_the_bias_at_order_one():
+    """The step-size rule aims the next step's error estimate at 1/BIAS_q of
+    the tolerance: a local error that scales as h^(q+1) and a new step of
+    h (BIAS E)^(-1/(q+1)) leave E' = 1/BIAS. On y' = -y with order 1 (the
+    error in the error-test norm, with weights rtol |y|, then stays constant
+    from step to step) the estimates after the first step change must sit at
+    1/6 once the step history holds the new step only."""
+    y, s, st, log = oracle.linear_integrate_steps(np.array([[-1.0]]), np.zeros((1, 1)), [1.0], 0.0, 5.0,
+                                                  rtol=1e-6, atol=1e-14, max_order=1)
+    assert s == 0 and np.all(log[:, 2] == 1)
+    h = log[:, 1]
+    changes = [k for k in range(1, len(h) - 1) if abs(h[k] / h[k - 1] - 1.0) > 1e-12]
+    assert changes, "no step change to check"
+    k0 = changes[0]
+    eta = h[k0] / h[k0 - 1]
+    assert 1.5 <= eta < 1e4  # a change neither below the threshold nor at the first-change cap
+    E = _settled_estimate(log, k0, 1)
+    assert len(E) > 100
+    np.testing.assert_allclose(E, 1.0 / 6.0, rtol=2e-3)
+
+
+def test_order_raise_targets_the_raised_bias():
+    """An order raise is taken with the order-(q+1) estimate and its own bias
+    (10) and exponent 1/(q+2): once the history has settled at the new order,
+    the order-2 estimates of y' = -y sit at 1/10."""
+    y, s, st, log = oracle.linear_integrate_steps(np.array([[-1.0]]), np.zeros((1, 1)), [1.0], 0.0, 5.0,
+                                                  rtol=1e-6, atol=1e-14, max_order=2)
+    assert s == 0
+    h, q = log[:, 1], log[:, 2]
+    raises = [k for k in range(1, len(h) - 1) if q[k] == 2 and q[k - 1] == 1]
+    assert raises, "no order raise"
+    k0 = raises[0]
+    assert abs(h[k0] / h[k0 - 1] - 1.0) > 1e-12  # the raise came with a step change
+    E = _settled_estimate(log, k0, 8)
+    assert len(E) > 100
+    np.testing.assert_allclose(E, 1.0 / 10.0, rtol=1e-2)
