@@ -481,8 +481,8 @@ def timed_steps(step, steps, warmup, stream, flush, barrier, rank, local, sample
     """W untimed and K timed steps, CUDA events on the launching stream, a
     barrier and a device synchronize on both sides, L2 flushed before each.
     With budget_s, at most 3 warm-up steps run and K is cut to what the last
-    warm-up step's time fits in budget_s (at least 3; the same on every rank);
-    the count actually timed is returned."""
+    warm-up step's time fits in budget_s (never below 3, never above the K
+    asked for; the same on every rank); the count actually timed is returned."""
     import torch
     import paper_2608_06466_b300 as mc
     if budget_s is not None:
@@ -496,7 +496,7 @@ def timed_steps(step, steps, warmup, stream, flush, barrier, rank, local, sample
     if budget_s is not None and t_last > 0.0:
         fit = int(max_over_ranks(budget_s / t_last, world, "cuda") if world == 1 else
                   -max_over_ranks(-budget_s / t_last, world, "cuda"))
-        steps = max(3, min(steps, fit))
+        steps = min(steps, max(3, fit))
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
