@@ -70,13 +70,13 @@ def test_synthetic_networks(mc, make, n, lu):
 def test_full_size_sampled(mc, lu, n_log2, variant):
     """The 13-ODE network at the workloads' full sizes in the launch
     configurations the benchmark times: the FP32-matrix persistent path on
-    2^22 cells (its headline) and the plain FP64 path on 2^20 cells; 512
+    2^22 cells (its headline) and the plain FP64 path on 2^20 cells; 4096
     sampled cells recomputed by the oracle."""
     net = network_13()
     n = 1 << n_log2
     cells = synthetic_cells(net, n, seed=3)
     gx, gT, gs, gst = _run(mc, net, cells, 1e10, lu_precision=lu, variant=variant)
-    idx = np.sort(np.random.default_rng(0).choice(n, 512, replace=False))
+    idx = np.sort(np.random.default_rng(0).choice(n, 4096, replace=False))
     ox, oT, os_, ost, stable, tight, rp = _reference(net, cells, 1e10, index=idx)
     rep = compare(gx[:, idx], gT[idx], gs[idx], ox, oT, os_, ost, stable=stable, tight=tight, reprobe=rp)
     print(lu, n, rep)
