@@ -538,7 +538,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="precision", choices=["precision", "mixed"])
     ap.add_argument("--cells", type=int, default=N_CELLS)
-    ap.add_argument("--max-timed-s", type=float, default=300.0,
+    ap.add_argument("--max-timed-s", type=float, default=100.0,
                     help="cut the timed steps to what fits this many seconds (at least 3) and the warm-up to 3; "
                          "0 times exactly --steps after exactly --warmup")
     ap.add_argument("--no-cpu-baseline", action="store_true")

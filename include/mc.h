@@ -112,8 +112,11 @@ typedef struct {
     double atol;            /* absolute tolerance (default 1e-10) */
     int32_t max_order;      /* highest BDF order, 1..5 (default 5) */
     int32_t max_steps;      /* step cap per cell, counting rejected attempts (default 100000) */
-    int32_t lu_precision;   /* 64: FP64 iteration matrix; 32: FP32 matrix and LU,
-                               FP64 residual/history/norm, failed cells retried in FP64 */
+    int32_t lu_precision;   /* 64: FP64 iteration matrix; 32: FP32 matrix and LU, solves
+                               refined with FP64 residuals, FP64 history/norm/EOS; a cell
+                               whose refinement cannot reach the FP64 solve is retried in
+                               FP64 (thread-per-cell) or switches to FP64 factors in place
+                               (networks above 16 ODEs, warp-per-cell) */
     int32_t variant;        /* MC_VARIANT_* */
     int32_t block_threads;  /* threads per block, 0 = autotuned */
     int32_t blocks_per_sm;  /* persistent grid = blocks_per_sm x SMs, 0 = autotuned */
