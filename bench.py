@@ -190,8 +190,16 @@ def parity_sample(net, cells, idx, gx, gT, gs):
     relT_all = None
     if gT is not None and o[1] is not None and both.any():
         relT_all = float((np.abs(gT[both] - o[1][both]) / np.abs(o[1][both])).max())
+    # the same figure for the oracle's own rounding twin (the same algorithm with
+    # FMA contraction): how far two correct integrations of these cells can differ
+    tw = oracle.oracle.rounding_twin()
+    w = tw.burn(tw.OracleNetwork(net), cells, DT, index=idx)
+    both_t = (w[2] == 0) & (o[2] == 0)
+    bt = np.abs(o[0][:, both_t]) > 1e-9
+    rel_twin = float((np.abs(w[0][:, both_t] - o[0][:, both_t])[bt] / np.abs(o[0][:, both_t])[bt]).max()) \
+        if bt.any() else 0.0
     return {"sampled_cells": int(idx.size), "pass": rep["pass"], "stable": rep["stable"],
-            "max_rel_x_all": rel_all, "max_rel_T_all": relT_all,
+            "max_rel_x_all": rel_all, "max_rel_T_all": relT_all, "max_rel_x_all_oracle_twin": rel_twin,
             "sensitive": rep["sensitive"], "reclassified": rep["reclassified"],
             "max_rel_x_stable": rep["max_rel_x_stable"], "max_rel_T_stable": rep.get("max_rel_T_stable"),
             "status_mismatch": rep["status_mismatch"],

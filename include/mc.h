@@ -121,7 +121,7 @@ typedef struct {
     int32_t block_threads;  /* threads per block, 0 = autotuned */
     int32_t blocks_per_sm;  /* persistent grid = blocks_per_sm x SMs, 0 = autotuned */
     int32_t straggler_steps;/* persistent variant: a cell still running after this many
-                               attempts is finished by a whole warp (0 = default 2048,
+                               attempts is finished by a whole warp (0 = default 8192,
                                -1 = never) */
     int32_t jacobian;       /* MC_JAC_ANALYTIC (default) or MC_JAC_FD: forward differences,
                                column j = (f(y + d_j e_j) - f(y)) / d_j,

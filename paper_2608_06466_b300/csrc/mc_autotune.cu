@@ -1,5 +1,5 @@
 // mc_autotune.cu -- measured launch-shape selection. mc_autotune times
-// candidates on a sample of the caller's cells in three rounds -- variant x
+// candidates on a sample of the caller's cells in three passes -- variant x
 // threads per block x persistent blocks per SM; then, for a thread-per-cell
 // persistent winner, the staging of the matrix work (the warp's shared memory
 // or the lane's own state); then the straggler hand-off threshold -- and
@@ -21,6 +21,11 @@
 using namespace mc;
 
 namespace {
+// default straggler hand-off threshold (attempts): on 2^22 net13 cells the
+// fused burn took 30.6 s handing off at 2048 attempts, 29.9 s at 8192, and
+// 46.7 s with no hand-off (the cells that run to the step cap then finish one
+// lane at a time after the bulk)
+constexpr int kHandoff = 8192;
 using Key = std::tuple<std::string, int, int, int, int>;
 std::mutex g_mu;
 std::map<Key, Tuned> g_table;
@@ -79,7 +84,7 @@ void save_entry(const Key &k, const Tuned &t) {
 Tuned mc::autotune_pick(const mc_network *net, const mc_burn_opts &o) {
   // defaults: thread-per-cell with hand-off for small networks, warp-per-cell
   // above 16 ODEs (the per-cell matrices no longer fit a lane's share of L1)
-  Tuned t{(net && net->n > 16) ? MC_VARIANT_WARP : MC_VARIANT_PERSISTENT, 128, 2, 2048, MC_STAGING_SHARED};
+  Tuned t{(net && net->n > 16) ? MC_VARIANT_WARP : MC_VARIANT_PERSISTENT, 128, 2, kHandoff, MC_STAGING_SHARED};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();
@@ -148,7 +153,7 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
     return true;
   };
   float best_ms = 1e30f;
-  Cand win{MC_VARIANT_PLAIN, 64, 0, MC_STAGING_SHARED, 2048};
+  Cand win{MC_VARIANT_PLAIN, 64, 0, MC_STAGING_SHARED, kHandoff};
   bool failed = false;
   auto consider = [&](const Cand &c) {
     if (failed) return;
@@ -162,17 +167,17 @@ extern "C" mc_status mc_autotune(const mc_network *net, const mc_burn_opts *opts
       win = c;
     }
   };
-  // round 1: variant x threads x blocks per SM
-  for (int thr : {64, 128, 256}) consider({MC_VARIANT_PLAIN, thr, 0, MC_STAGING_SHARED, 2048});
+  // first pass: variant x threads x blocks per SM
+  for (int thr : {64, 128, 256}) consider({MC_VARIANT_PLAIN, thr, 0, MC_STAGING_SHARED, kHandoff});
   for (int thr : {64, 128, 256})
-    for (int bps : {1, 2, 4}) consider({MC_VARIANT_PERSISTENT, thr, bps, MC_STAGING_SHARED, 2048});
-  for (int bps : {1, 2, 4}) consider({MC_VARIANT_WARP, 128, bps, MC_STAGING_SHARED, 2048});
+    for (int bps : {1, 2, 4}) consider({MC_VARIANT_PERSISTENT, thr, bps, MC_STAGING_SHARED, kHandoff});
+  for (int bps : {1, 2, 4}) consider({MC_VARIANT_WARP, 128, bps, MC_STAGING_SHARED, kHandoff});
   if (win.var == MC_VARIANT_PERSISTENT) {
-    // round 2: staging of the matrix work; round 3: hand-off threshold
+    // second pass: staging of the matrix work; third: hand-off threshold
     Cand c = win;
     c.stg = MC_STAGING_LANE;
     consider(c);
-    for (int strag : {512, 8192, -1}) {
+    for (int strag : {2048, 32768, -1}) {
       c = win;
       c.strag = strag;
       consider(c);
