@@ -2,7 +2,8 @@
 -DMC_BOUNDS_CHECK). Every launch form runs on small cases in a child process
 that loads the check build; its record must show no refused access and every
 cell of every verified call stored exactly once, and its results must equal
-the normal build's bit for bit (the checks change no arithmetic)."""
+the normal build's, run the same way in another fresh process, bit for bit
+(the checks change no arithmetic)."""
 import importlib.util
 import os
 import subprocess
@@ -24,16 +25,21 @@ def _build_check_library():
     return mod.build(check=True)
 
 
+def _run_cases(lib, out):
+    """bounds_case.py in a fresh process with the library lib (so that no
+    state of this process -- autotuner picks, scratch -- reaches it)."""
+    env = dict(os.environ, MC_LIBRARY=lib)
+    r = subprocess.run([sys.executable, CASE, str(out)], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-4000:]
+    return dict(np.load(out))
+
+
 def test_bounds_check_build_is_clean_and_matches(tmp_path):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    lib = _build_check_library()
-    out = tmp_path / "check.npz"
-    env = dict(os.environ, MC_LIBRARY=lib)
-    r = subprocess.run([sys.executable, CASE, str(out)], env=env, capture_output=True, text=True, timeout=900)
-    assert r.returncode == 0, r.stderr[-4000:]
-    chk = dict(np.load(out))
+    check_lib = _build_check_library()
+    chk = _run_cases(check_lib, tmp_path / "check.npz")
     assert str(chk["library"]).endswith("libmc_check.so")
     rep = {k[len("report."):]: int(v) for k, v in chk.items() if k.startswith("report.")}
     assert rep["enabled"] == 1
@@ -44,17 +50,18 @@ def test_bounds_check_build_is_clean_and_matches(tmp_path):
     assert rep["cells_checked"] == sum(n for _, n in bounds_case.VERIFIED), rep
     assert rep["cells_not_once"] == 0, rep
 
-    import paper_2608_06466_b300 as mc
-    assert mc.mc_bounds_report(0)["enabled"] == 0  # the normal build checks nothing
-    ref = bounds_case.run_cases(mc)
+    ref = _run_cases(os.path.join(ROOT, "paper_2608_06466_b300", "libmc.so"), tmp_path / "normal.npz")
+    assert str(ref["library"]).endswith("libmc.so")
+    assert int(ref["report.enabled"]) == 0  # the normal build checks nothing
     # bitwise equality needs a schedule-free hand-off: fewer cells reach the
     # threshold than the record list holds (a full list leaves the choice of
     # cells to timing, and thread and warp forms round differently)
     sx = ref["fused.sx"][:, :4096].astype(np.int64)
     assert int(((sx[0] + sx[1] + sx[2]) >= bounds_case.HANDOFF).sum()) < bounds_case.HANDOFF_CAP
-    assert set(ref) == {k for k in chk if "." in k and not k.startswith("report.")}
-    for k, v in ref.items():
-        np.testing.assert_array_equal(chk[k], v, err_msg=k)
+    keys = {k for k in ref if "." in k and not k.startswith("report.")}
+    assert keys == {k for k in chk if "." in k and not k.startswith("report.")}
+    for k in sorted(keys):
+        np.testing.assert_array_equal(chk[k], ref[k], err_msg=k)
     # every cell got a status; padding past n untouched
     for name, n in bounds_case.VERIFIED:
         st = ref[f"{name}.st"]
