@@ -125,8 +125,8 @@ typedef struct {
                                -1 = never) */
     int32_t jacobian;       /* MC_JAC_ANALYTIC (default) or MC_JAC_FD: forward differences,
                                column j = (f(y + d_j e_j) - f(y)) / d_j,
-                               d_j = 2^-26 (|y_j| + atol / rtol) (one of the "Jacobian
-                               approximations" of the paper's retry, Software design ¶3) */
+                               d_j = 2^-26 (|y_j| + atol / rtol) (an approximate
+                               Jacobian for the paper's per-zone retry, Software design ¶3) */
     int32_t staging;        /* where a thread-per-cell lane's Jacobian and LU are computed:
                                MC_STAGING_SHARED, the whole warp in the warp's shared-memory
                                workspace; MC_STAGING_LANE, the lane alone in its own state;
@@ -191,8 +191,8 @@ typedef struct {
                              RKC rung is a plain RKC burn */
 
 /* Burn with a retry ladder (paper: Software design section, paragraph 3 --
- * a zone whose integration fails is retried with different tolerances or
- * Jacobian approximations before the failure is passed back). Every cell is
+ * a zone whose integration fails is integrated again under other tolerances
+ * or with an approximate Jacobian before the failure is passed back). Every cell is
  * burned with rung 0; a cell whose status is MC_CELL_MAX_STEPS,
  * MC_CELL_H_UNDERFLOW, MC_CELL_CONV_FAIL or MC_CELL_NONFINITE is burned again
  * from its inputs with the next rung, up to n_rungs (1..8). Outputs, status

@@ -35,8 +35,9 @@
  * 1/BIAS_q = 1/6; after an order raise at 1/BIAS_q+1 = 1/10), the Jacobian
  * against finite differences, and the LU against the definition.
  *
- * Failure retry (same paragraph 3: retry a zone with different tolerances or
- * Jacobian approximations): a forward-difference Jacobian (pinned exact on a
+ * Failure retry (same paragraph 3: a failed zone may be integrated again under
+ * other tolerances or with an approximate Jacobian): a forward-difference
+ * Jacobian (pinned exact on a
  * linear chain up to rounding, to its closed-form error on Robertson, to the
  * analytic Jacobian, and through Robertson's published values) and a per-cell
  * retry ladder (pinned against the plain burn of each rung).
@@ -1211,7 +1212,7 @@ int or_net_eval(const or_net *net, double ndens, double T_iso, const double *ks,
     return 0;
 }
 
-/* Forward-difference Jacobian: one of the "Jacobian approximations" the     */
+/* Forward-difference Jacobian: an approximate Jacobian of the kind the      */
 /* paper's failure policy may retry with (Software design section, ¶3). The  */
 /* paper gives no formula; this is the plain one-sided difference           */
 /*   J[:, j] = (f(y + d_j e_j) - f(y)) / d_j,                                 */
@@ -1365,11 +1366,12 @@ int or_burn_batch_src(const or_net *net, double rtol, double atol, int max_order
 
 /* ------------------------------------------------------------------------ */
 /* Retry ladder (Software design section, ¶3: a zone whose integration fails */
-/* may be retried on its own with different tolerances or Jacobian           */
-/* approximations, or the failure handed back). Each cell is burned from its */
-/* inputs with rung 0; while it fails with a status a retry can change       */
-/* (step cap, step-size underflow, Newton failures, non-finite state) and    */
-/* rungs remain, it is burned again from the same inputs with the next rung. */
+/* may be integrated again on its own under other tolerances or with an      */
+/* approximate Jacobian, or the failure handed back). Each cell is burned    */
+/* from its inputs with rung 0; while it fails with a status a retry can     */
+/* change (step cap, step-size underflow, Newton failures, non-finite      */
+/* state) and rungs remain, it is burned again from the same inputs with    */
+/* the next rung.                                                            */
 /* The outputs are those of the last attempt, rung[c] says which rung gave   */
 /* them. Rejected inputs are never retried.                                  */
 /* ------------------------------------------------------------------------ */

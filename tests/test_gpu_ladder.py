@@ -1,6 +1,6 @@
 """The retry ladder (mc_burn_ladder) and the RKC integrator on the GPU against
 the CPU oracle (Software design section: paragraph 3, a zone that fails is
-retried with different tolerances or Jacobian approximations; paragraphs 2
+integrated again under other tolerances or with an approximate Jacobian; paragraphs 2
 and 4, RKC beside VODE on the same network interface)."""
 import numpy as np
 import pytest

@@ -1,6 +1,6 @@
 """Pins for the oracle's failure-retry pieces (Software design section, ¶3: a
-zone whose integration fails may be retried on its own with different
-tolerances or Jacobian approximations): the forward-difference Jacobian and
+zone whose integration fails may be integrated again on its own under other
+tolerances or with an approximate Jacobian): the forward-difference Jacobian and
 the retry ladder. Each check is against something other than the code under
 test -- a closed form, exactness on a linear system, published values, or the
 oracle's plain burn."""
