@@ -64,3 +64,22 @@ def test_network_create_rejects_bad_descriptions_without_gpu():
     except mc.MCError as e:
         raised = "MC_E_UNSUPPORTED" in str(e)
     assert raised
+
+
+@pytest.mark.parametrize("field,value,message", [
+    ("staging", 3, "staging must be"), ("staging", -1, "staging must be"),
+    ("jacobian", 2, "jacobian must be"), ("lu_precision", 16, "lu_precision must be"),
+    ("max_order", 6, "max_order must be"), ("rtol", 0.0, "rtol and atol"),
+    ("straggler_steps", -2, "straggler_steps"), ("block_threads", 48, "block_threads"),
+])
+def test_burn_options_are_checked_before_any_device_call(field, value, message):
+    """Option validation runs first: a bad field is refused with its own message
+    on a machine without a GPU (no network is needed to get there)."""
+    import types
+    import paper_2608_06466_b300 as mc
+    o = mc.mc_burn_opts_default()
+    setattr(o, field, value)
+    dummy = types.SimpleNamespace(handle=None)
+    with pytest.raises(mc.MCError, match="MC_E_INVALID") as err:
+        mc.mc_burn_batch(dummy, o, 0, 1.0, None, 0, None, None, None, None, None)
+    assert message in str(err.value) or message in mc.mc_last_error()
