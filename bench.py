@@ -259,9 +259,7 @@ def serving_measurement(mc, window_s=40.0, seed=7, edge_range=(16, 48), concurre
         for rid in list(live):
             rc, info = srv.poll(rid)
             if rc == 0:
-                t = _t.perf_counter() - t0
-                if t <= window_s:
-                    done.append((t, live[rid][1]))
+                done.append((_t.perf_counter() - t0, live[rid][1]))
                 del live[rid]
         if not live and now >= window_s:
             break
@@ -269,11 +267,14 @@ def serving_measurement(mc, window_s=40.0, seed=7, edge_range=(16, 48), concurre
     srv.drain(3600)
     srv.close()
     done.sort()
-    done_n = len(done)
+    inside = [d for d in done if d[0] <= window_s]
+    done_n = len(inside)
     if done_n >= 2:
-        lam_cells = sum(c for _, c in done[1:]) / max(window_s - done[0][0], 1e-9)
+        lam_cells = sum(c for _, c in inside[1:]) / max(window_s - inside[0][0], 1e-9)
     else:
-        lam_cells = sum(c for _, c in done) / window_s
+        # too short a window for the steady-state estimate: every request over
+        # the time to the last completion
+        lam_cells = sum(c for _, c in done) / max(done[-1][0], 1e-9)
     mean_cells = float(np.mean([r["n_cells"] for r in pool]))
     out = {"lambda_sat_cells_per_s": lam_cells, "saturation_requests_completed": done_n,
            "mean_cells_per_request": mean_cells, "edge_range": list(edge_range), "window_s": window_s,
