@@ -207,6 +207,22 @@ def parity_sample(net, cells, idx, gx, gT, gs):
             "sensitive_err_oracle_p50_p90_max": rep.get("sensitive_err_oracle_p50_p90_max")}
 
 
+def steady_throughput(done, window_s):
+    """Cells per second of a closed loop from its completions [(time, cells)]:
+    the cells completed after the first completion and inside the window,
+    over the time between the two (the ramp-up before the first completion
+    and the work in flight at the window's end are left out). With fewer than
+    two completions inside the window, every request over the time to the
+    last completion. Returns (cells/s, completions inside the window)."""
+    done = sorted(done)
+    inside = [d for d in done if d[0] <= window_s]
+    if len(inside) >= 2:
+        return sum(c for _, c in inside[1:]) / max(window_s - inside[0][0], 1e-9), len(inside)
+    if not done:
+        return 0.0, 0
+    return sum(c for _, c in done) / max(done[-1][0], 1e-9), len(inside)
+
+
 def serving_measurement(mc, window_s=40.0, seed=7, edge_range=(16, 48), concurrency=8):
     """Serving loop on AMR-box requests (edge L log-uniform in edge_range,
     cells = L^3, 50/50 net13 / net33, FP32 iteration matrix, 150 GB budget).
@@ -266,19 +282,13 @@ def serving_measurement(mc, window_s=40.0, seed=7, edge_range=(16, 48), concurre
         _t.sleep(0.002)
     srv.drain(3600)
     srv.close()
-    done.sort()
-    inside = [d for d in done if d[0] <= window_s]
-    done_n = len(inside)
-    if done_n >= 2:
-        lam_cells = sum(c for _, c in inside[1:]) / max(window_s - inside[0][0], 1e-9)
-    else:
-        # too short a window for the steady-state estimate: every request over
-        # the time to the last completion
-        lam_cells = sum(c for _, c in done) / max(done[-1][0], 1e-9)
+    lam_cells, done_n = steady_throughput(done, window_s)
     mean_cells = float(np.mean([r["n_cells"] for r in pool]))
     out = {"lambda_sat_cells_per_s": lam_cells, "saturation_requests_completed": done_n,
            "mean_cells_per_request": mean_cells, "edge_range": list(edge_range), "window_s": window_s,
            "concurrency": concurrency, "lu_precision": 32, "loads": []}
+    if not lam_cells > 0.0:
+        return out  # nothing completed: no load levels to offer
     for load in (0.5, 0.9):
         rate = load * lam_cells / mean_cells
         reqs = box_request_stream(max(1, int(rate * window_s * 3) + 8), rate, seed=seed + int(load * 100),
